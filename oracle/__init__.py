@@ -1,0 +1,467 @@
+"""FP64 CPU oracle for multi-slice fusion (arXiv 2008.01567).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA library is
+checked against.  Only tests/, the smoke check and the benchmark's CPU-baseline
+leg may import it.  It shares no code with the CUDA path; the loop-heavy parts
+(projector, phantom, q-GGMRF ICD) are plain C in oracle.c, the rest is numpy in
+float64 written in the paper's order and notation.
+
+Every function names the passage it follows.  Readings of points the paper leaves
+open (projector model, CNN depth and width, temporal edges, ...) are listed in
+the design doc.  All functions here are pinned by tests under tests/ against closed
+forms, invariants, brute force or library routines; none is marked unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        D, I, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        lib.or_project.argtypes = [P, P, I, I, I, D, I, I, D, D, D, D, P, I, I]
+        lib.or_ellipsoid_project.argtypes = [P, I, P, I, I, D, D, D, D, P, I]
+        lib.or_ellipsoid_voxelize.argtypes = [P, I, P, I, I, I, D, I]
+        lib.or_qggmrf_rho.argtypes = [D, D, D, D, D]
+        lib.or_qggmrf_rho.restype = D
+        lib.or_qggmrf_coef.argtypes = [D, D, D, D, D]
+        lib.or_qggmrf_coef.restype = D
+        lib.or_qggmrf_cost.argtypes = [P, I, I, I, I, D, D, D, D, D]
+        lib.or_qggmrf_cost.restype = D
+        lib.or_qggmrf_icd.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, I]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ====================================================================== Sec. II
+# Measurement model: y_n = A_n x_n + noise, l(x) = 1/2 sum_n ||y_n - A_n x_n||^2_Lambda_n.
+
+
+def project(x3: np.ndarray, scan, angles: np.ndarray) -> np.ndarray:
+    """y = A_n x_n for one frame (Sec. II, Eq. (2)); x3 [nz,ny,nx] -> y [views,nv,nu]."""
+    x3 = np.ascontiguousarray(x3, dtype=np.float64)
+    angles = np.ascontiguousarray(angles, dtype=np.float64)
+    y = np.zeros((len(angles), scan.nv, scan.nu))
+    nz, ny, nx = x3.shape
+    _L().or_project(_p(x3), _p(y), nx, ny, nz, scan.vox, scan.nu, scan.nv, scan.pitch,
+                    scan.pitch, scan.dso, scan.dsd, _p(angles), len(angles), 0)
+    return y
+
+
+def backproject(y3: np.ndarray, scan, angles: np.ndarray, shape=None) -> np.ndarray:
+    """x = A_n^T y_n for one frame: the literal transpose (scatter) of `project`."""
+    y3 = np.ascontiguousarray(y3, dtype=np.float64)
+    angles = np.ascontiguousarray(angles, dtype=np.float64)
+    nz, ny, nx = shape if shape is not None else (scan.n, scan.n, scan.n)
+    x = np.zeros((nz, ny, nx))
+    _L().or_project(_p(x), _p(y3), nx, ny, nz, scan.vox, scan.nu, scan.nv, scan.pitch,
+                    scan.pitch, scan.dso, scan.dsd, _p(angles), len(angles), 1)
+    return x
+
+
+def project4d(x4: np.ndarray, scan) -> np.ndarray:
+    """A x for the whole 4D volume: frames are independent (Eq. (2) is separable)."""
+    ang = scan.angles()
+    return np.stack([project(x4[t], scan, ang[t]) for t in range(x4.shape[0])])
+
+
+def backproject4d(y4: np.ndarray, scan, shape3=None) -> np.ndarray:
+    ang = scan.angles()
+    return np.stack([backproject(y4[t], scan, ang[t], shape3) for t in range(y4.shape[0])])
+
+
+def ellipsoid_sinogram(ell4: np.ndarray, scan) -> np.ndarray:
+    """Exact line integrals of the ellipsoid phantom, frame by frame -> [nt,V,nv,nu]."""
+    ang = scan.angles()
+    out = np.zeros((scan.nt, scan.views, scan.nv, scan.nu))
+    for t in range(scan.nt):
+        e = np.ascontiguousarray(ell4[t], dtype=np.float64)
+        a = np.ascontiguousarray(ang[t])
+        _L().or_ellipsoid_project(_p(e), e.shape[0], _p(out[t]), scan.nu, scan.nv, scan.pitch,
+                                  scan.pitch, scan.dso, scan.dsd, _p(a), scan.views)
+    return out
+
+
+def ellipsoid_volume(ell4: np.ndarray, scan, ss: int = 4) -> np.ndarray:
+    """Supersampled voxelisation of the phantom -> [nt,n,n,n]."""
+    out = np.zeros((scan.nt, scan.n, scan.n, scan.n))
+    for t in range(scan.nt):
+        e = np.ascontiguousarray(ell4[t], dtype=np.float64)
+        _L().or_ellipsoid_voxelize(_p(e), e.shape[0], _p(out[t]), scan.n, scan.n, scan.n, scan.vox, ss)
+    return out
+
+
+def expected_counts(p: np.ndarray, I0: float) -> np.ndarray:
+    """Beer-Lambert mean photon count I0 exp(-p) for line integrals p."""
+    return I0 * np.exp(-p)
+
+
+def log_measurement(counts: np.ndarray, I0: float) -> np.ndarray:
+    """y = -ln(max(n,1)/I0): zero counts are clamped to one photon."""
+    return -np.log(np.maximum(counts, 1.0) / I0)
+
+
+def weights(y: np.ndarray, c: float) -> np.ndarray:
+    """Lambda_n = diag{c exp(-y_n)} (Sec. II, below Eq. (2))."""
+    return c * np.exp(-y)
+
+
+# ====================================================================== Sec. III
+# Data proximal map L(x) = argmin_z l(z) + ||x - z||^2 / (2 sigma^2)   (Eq. (4)).
+
+
+def normal_op(z3, lam3, scan, angles, sigma):
+    """(A^T Lambda A + I/sigma^2) z for one frame: the Hessian of the cost in Eq. (4)."""
+    return backproject(lam3 * project(z3, scan, angles), scan, angles, z3.shape) + z3 / sigma ** 2
+
+
+def prox_data_frame(y3, lam3, v3, z3, scan, angles, sigma, n_cg):
+    """Partial update L~(v; z) of Eq. (13): n_cg conjugate-gradient iterations on
+    (A^T Lambda A + I/sigma^2) z = A^T Lambda y + v/sigma^2, warm-started at z.
+    Textbook Hestenes-Stiefel CG; the scalars are kept per frame."""
+    z = np.array(z3, dtype=np.float64)
+    r = backproject(lam3 * (y3 - project(z, scan, angles)), scan, angles, z.shape) + (v3 - z) / sigma ** 2
+    p = r.copy()
+    rr = float(np.vdot(r, r))
+    for _ in range(n_cg):
+        q = normal_op(p, lam3, scan, angles, sigma)
+        pq = float(np.vdot(p, q))
+        if pq == 0.0:
+            break
+        alpha = rr / pq
+        z += alpha * p
+        r -= alpha * q
+        rr_new = float(np.vdot(r, r))
+        beta = rr_new / rr if rr != 0.0 else 0.0
+        p = r + beta * p
+        rr = rr_new
+    return z
+
+
+def prox_data(y4, lam4, v4, z4, scan, sigma, n_cg):
+    """L~ for the 4D volume: one independent CG per time-point (Eq. (2) separable, Sec. VI)."""
+    ang = scan.angles()
+    return np.stack([prox_data_frame(y4[t], lam4[t], v4[t], z4[t], scan, ang[t], sigma, n_cg)
+                     for t in range(v4.shape[0])])
+
+
+# Prior proximal map H(x) = argmin_z ||x - z||^2/(2 sigma^2) + h(z)   (Eq. (5)),
+# with h the 4D q-GGMRF MRF of Sec. VII (26 spatial + 2 temporal neighbours).
+
+
+def qggmrf_rho(d, p, q, T, sx):
+    return _L().or_qggmrf_rho(float(d), p, q, T, sx)
+
+
+def qggmrf_coef(d, p, q, T, sx):
+    return _L().or_qggmrf_coef(float(d), p, q, T, sx)
+
+
+def qggmrf_cost(z4, p, q, T, sx, bt):
+    z4 = np.ascontiguousarray(z4, dtype=np.float64)
+    nt, nz, ny, nx = z4.shape
+    return _L().or_qggmrf_cost(_p(z4), nx, ny, nz, nt, p, q, T, sx, bt)
+
+
+def prox_qggmrf(v4, z4, sigma, p, q, T, sx, bt, n_sweeps):
+    """n_sweeps 16-colour ICD sweeps for H(v), starting from z4 (see oracle.c)."""
+    v4 = np.ascontiguousarray(v4, dtype=np.float64)
+    z = np.array(z4, dtype=np.float64, order="C")
+    nt, nz, ny, nx = v4.shape
+    _L().or_qggmrf_icd(_p(v4), _p(z), nx, ny, nz, nt, sigma, p, q, T, sx, bt, n_sweeps)
+    return z
+
+
+# MACE operators.
+
+
+def mu_from_beta(beta: float, K: int) -> np.ndarray:
+    """Agent weights of the average in Eq. (9): mu_0 = 1/(1+beta), mu_k = beta/((1+beta)K)."""
+    return np.array([1.0 / (1.0 + beta)] + [beta / ((1.0 + beta) * K)] * K)
+
+
+def average(W, mu):
+    """W-bar of Eq. (9) as the weighted sum sum_i mu_i W_i."""
+    return sum(m * w for m, w in zip(mu, W))
+
+
+def G(W, mu):
+    """Averaging operator of Eq. (8): every block becomes W-bar."""
+    wb = average(W, mu)
+    return [wb.copy() for _ in W]
+
+
+def mann_step_direct(W, FW, mu, rho):
+    """Eq. (12): W <- (1-rho) W + rho T W with T = (2G - I)(2F - I), given F(W)."""
+    V = [2.0 * f - w for f, w in zip(FW, W)]
+    GV = G(V, mu)
+    TW = [2.0 * g - v for g, v in zip(GV, V)]
+    return [(1.0 - rho) * w + rho * t for w, t in zip(W, TW)]
+
+
+def mace_iteration(W, X, agents, mu, rho):
+    """One pass of Algorithm 1: X <- F~(W; X); Z <- G(2X - W); W <- W + 2 rho (Z - X).
+
+    agents[i](W_i, X_i) returns the new X_i (agent 0 is the partial-update data
+    prox L~, the others the prior agents H_k).  Returns (W, X, residual)."""
+    X = [agents[i](W[i], X[i]) for i in range(len(W))]
+    zbar = average([2.0 * x - w for x, w in zip(X, W)], mu)
+    W = [w + 2.0 * rho * (zbar - x) for w, x in zip(W, X)]
+    return W, X, consensus_residual(X, mu)
+
+
+def consensus_residual(X, mu):
+    """sqrt(sum_i mu_i ||X_i - X-bar||^2) / ||X-bar||: the spread between the agents'
+    states that the stopping rule of Sec. III compares with a threshold."""
+    xb = average(X, mu)
+    num = sum(m * float(np.vdot(x - xb, x - xb)) for m, x in zip(mu, X))
+    den = float(np.vdot(xb, xb))
+    return math.sqrt(num / den) if den > 0 else math.sqrt(num)
+
+
+def mace(x0, agents, mu, rho, n_iter):
+    """Algorithm 1 from X = W = [x0; ...; x0]; returns (X_0, W, X, residuals)."""
+    W = [np.array(x0, dtype=np.float64) for _ in agents]
+    X = [np.array(x0, dtype=np.float64) for _ in agents]
+    res = []
+    for _ in range(n_iter):
+        W, X, r = mace_iteration(W, X, agents, mu, rho)
+        res.append(r)
+    return X[0], W, X, res
+
+
+# Metrics (Sec. VII-A).
+
+
+def nrmse(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def psnr(x, ref):
+    """20 log10(Range(ref)/RMSE), Range = 99.9th minus 0.1st percentile of ref."""
+    rng = np.percentile(ref, 99.9) - np.percentile(ref, 0.1)
+    return 20.0 * math.log10(rng / math.sqrt(float(np.mean((x - ref) ** 2))))
+
+
+# ====================================================================== Sec. IV-V
+# 2.5D CNN denoiser: five adjacent time-points of a 2D slice enter as channels and
+# the denoised centre slice comes out, with a residual connection through the
+# centre channel.  Depth 10, 3x3 kernels, 64 channels, ReLU, BatchNorm in the
+# hidden layers (residual learning as in DnCNN).
+
+ORIENTS = ("xy", "yz", "zx")
+
+
+def orient_slices(v4: np.ndarray, orient: str) -> np.ndarray:
+    """4D [nt,nz,ny,nx] -> images [nt, S, H, W] in the plane of the agent:
+    xy-t: slice z, image (y, x); yz-t: slice x, image (z, y); zx-t: slice y, image (x, z)."""
+    if orient == "xy":
+        return v4
+    if orient == "yz":
+        return v4.transpose(0, 3, 1, 2)
+    if orient == "zx":
+        return v4.transpose(0, 2, 3, 1)
+    raise ValueError(orient)
+
+
+def orient_volume(s4: np.ndarray, orient: str) -> np.ndarray:
+    """Inverse of orient_slices."""
+    if orient == "xy":
+        return s4
+    if orient == "yz":
+        return s4.transpose(0, 2, 3, 1)
+    if orient == "zx":
+        return s4.transpose(0, 3, 1, 2)
+    raise ValueError(orient)
+
+
+def window5(s4: np.ndarray) -> np.ndarray:
+    """[nt,S,H,W] -> network input [nt*S, 5, H, W]: channels are time-points
+    t-2..t+2 of the same slice, clamped at the first and last time-point."""
+    nt = s4.shape[0]
+    idx = np.clip(np.arange(nt)[:, None] + np.arange(-2, 3)[None, :], 0, nt - 1)
+    x = s4[idx]                              # [nt, 5, S, H, W]
+    x = x.transpose(0, 2, 1, 3, 4)           # [nt, S, 5, H, W]
+    return np.ascontiguousarray(x.reshape(nt * s4.shape[1], 5, s4.shape[2], s4.shape[3]))
+
+
+def bf16(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def conv3x3(x, w, b=None):
+    """y[n,o,i,j] = b[o] + sum_{c,ky,kx} w[o,c,ky,kx] x[n,c,i+ky-1,j+kx-1], zero padding."""
+    n, c, h, wd = x.shape
+    xp = np.pad(x, ((0, 0), (0, 0), (1, 1), (1, 1)))
+    y = np.zeros((n, w.shape[0], h, wd))
+    for ky in range(3):
+        for kx in range(3):
+            y += np.tensordot(w[:, :, ky, kx], xp[:, :, ky:ky + h, kx:kx + wd], axes=([1], [1])).transpose(1, 0, 2, 3)
+    if b is not None:
+        y += b[None, :, None, None]
+    return y
+
+
+def conv3x3_dgrad(dy, w):
+    """Input gradient of conv3x3: correlation of dy with the flipped, transposed kernel."""
+    return conv3x3(dy, np.ascontiguousarray(w.transpose(1, 0, 2, 3)[:, :, ::-1, ::-1]))
+
+
+def conv3x3_wgrad(dy, x):
+    """Weight gradient of conv3x3: dw[o,c,ky,kx] = sum_{n,i,j} dy[n,o,i,j] x[n,c,i+ky-1,j+kx-1]."""
+    n, c, h, wd = x.shape
+    xp = np.pad(x, ((0, 0), (0, 0), (1, 1), (1, 1)))
+    dw = np.zeros((dy.shape[1], c, 3, 3))
+    for ky in range(3):
+        for kx in range(3):
+            dw[:, :, ky, kx] = np.tensordot(dy, xp[:, :, ky:ky + h, kx:kx + wd], axes=([0, 2, 3], [0, 2, 3]))
+    return dw
+
+
+BN_EPS = 1e-5
+
+
+def fold_bn(convs, bns, stats):
+    """Inference network with BatchNorm folded into the hidden convolutions:
+    w' = w * g/sqrt(var+eps), b' = (b - mean) g/sqrt(var+eps) + beta."""
+    out = [convs[0]]
+    for l in range(1, len(convs) - 1):
+        w, b = convs[l]
+        g, be = bns[l - 1]
+        mean, var = stats[l - 1]
+        s = g / np.sqrt(var + BN_EPS)
+        out.append((w * s[:, None, None, None], (b - mean) * s + be))
+    out.append(convs[-1])
+    return out
+
+
+def cnn_forward(x, layers, emulate_bf16=False):
+    """Inference forward of the 2.5D residual CNN with folded layers [(w, b)] on
+    x [B,5,H,W]; returns the denoised centre slice [B,H,W] = centre - R(x).
+    With emulate_bf16 the weights, the network input and every stored hidden
+    activation are rounded to bfloat16 (the accumulations stay FP64)."""
+    r = bf16 if emulate_bf16 else (lambda a: a)
+    a = r(x)
+    for l, (w, b) in enumerate(layers):
+        z = conv3x3(a, r(w), b)
+        if l < len(layers) - 1:
+            a = r(np.maximum(z, 0.0))
+        else:
+            a = z
+    return x[:, 2] - a[:, 0]
+
+
+def denoise(v4, layers, orient, emulate_bf16=False):
+    """Agent H_{orient,t} of Eq. (14) on a 4D volume [nt,nz,ny,nx]."""
+    s4 = orient_slices(v4, orient)
+    x = window5(s4)
+    out = cnn_forward(x, layers, emulate_bf16)
+    return np.ascontiguousarray(orient_volume(out.reshape(s4.shape), orient))
+
+
+# ---- training (Sec. V): MSE on (noisy, clean) pairs, BatchNorm in training mode, Adam.
+
+
+def train_forward(x, convs, bns):
+    """Training forward; returns (out, cache).  Hidden layers: conv (+bias),
+    BatchNorm with batch statistics (biased variance), ReLU."""
+    cache = {"a": [x], "z": [], "xhat": [], "istd": [], "y": [], "stats": []}
+    a = x
+    L = len(convs)
+    for l in range(L):
+        w, b = convs[l]
+        z = conv3x3(a, w, b)
+        cache["z"].append(z)
+        if l == 0:
+            a = np.maximum(z, 0.0)
+        elif l < L - 1:
+            g, be = bns[l - 1]
+            mean = z.mean(axis=(0, 2, 3))
+            var = z.var(axis=(0, 2, 3))
+            istd = 1.0 / np.sqrt(var + BN_EPS)
+            xhat = (z - mean[None, :, None, None]) * istd[None, :, None, None]
+            yv = g[None, :, None, None] * xhat + be[None, :, None, None]
+            cache["xhat"].append(xhat)
+            cache["istd"].append(istd)
+            cache["y"].append(yv)
+            cache["stats"].append((mean, var))
+            a = np.maximum(yv, 0.0)
+        else:
+            a = z
+        if l < L - 1:
+            cache["a"].append(a)
+    out = x[:, 2] - a[:, 0]
+    return out, cache
+
+
+def train_loss_grad(x, clean, convs, bns):
+    """MSE loss mean((out - clean)^2) and its gradients w.r.t. every conv weight,
+    conv bias and BatchNorm gamma/beta.  Returns (loss, gconvs, gbns, stats)."""
+    out, c = train_forward(x, convs, bns)
+    L = len(convs)
+    npx = out.size
+    loss = float(np.mean((out - clean) ** 2))
+    dout = 2.0 * (out - clean) / npx
+    da = -dout[:, None]                       # d/dR of out = centre - R
+    gconvs = [None] * L
+    gbns = [None] * (L - 2)
+    for l in range(L - 1, -1, -1):
+        if l == L - 1:
+            dz = da
+        elif l == 0:
+            dz = da * (c["z"][0] > 0)
+        else:
+            dy = da * (c["y"][l - 1] > 0)
+            xhat, istd = c["xhat"][l - 1], c["istd"][l - 1]
+            g = bns[l - 1][0]
+            gbns[l - 1] = ((dy * xhat).sum(axis=(0, 2, 3)), dy.sum(axis=(0, 2, 3)))
+            dxh = dy * g[None, :, None, None]
+            m1 = dxh.mean(axis=(0, 2, 3))[None, :, None, None]
+            m2 = (dxh * xhat).mean(axis=(0, 2, 3))[None, :, None, None]
+            dz = istd[None, :, None, None] * (dxh - m1 - xhat * m2)
+        a_in = c["a"][l]
+        gconvs[l] = (conv3x3_wgrad(dz, a_in), dz.sum(axis=(0, 2, 3)))
+        if l > 0:
+            da = conv3x3_dgrad(dz, convs[l][0])
+    return loss, gconvs, gbns, c["stats"]
+
+
+def adam_update(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015) with bias correction; t counts from 1."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -1,0 +1,207 @@
+"""Pins of the oracle's proximal agents and MACE loop (Sec. III, Eqs. (4)-(13),
+Algorithm 1) against dense brute-force solves, identities and finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2008_01567_gb300 import synth
+
+
+def _dense_A(oracle, sc, ang, shape):
+    n = int(np.prod(shape))
+    cols = []
+    for i in range(n):
+        e = np.zeros(n); e[i] = 1.0
+        cols.append(oracle.project(e.reshape(shape), sc, ang).ravel())
+    return np.stack(cols, axis=1)
+
+
+def _tiny_problem(oracle, n=4, nt=1, seed=0):
+    sc = synth.Scan(n=n, nt=nt, nu=7, nv=6, views=3)
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(0.1, 1.0, (nt, sc.views, sc.nv, sc.nu))
+    lam = oracle.weights(y, 50.0)
+    return sc, y, lam
+
+
+def test_cg_prox_equals_dense_solve(oracle):
+    # With as many CG steps as unknowns, L~(v; z) equals the exact proximal map of
+    # Eq. (4): (A^T Lambda A + I/sigma^2) z = A^T Lambda y + v/sigma^2.
+    sc, y, lam = _tiny_problem(oracle)
+    ang = sc.angles()[0]
+    shape = (4, 4, 4)
+    A = _dense_A(oracle, sc, ang, shape)
+    sigma = 0.3
+    v = synth.normal(1, shape)
+    z0 = synth.normal(2, shape)
+    H = A.T @ (lam[0].ravel()[:, None] * A) + np.eye(64) / sigma ** 2
+    rhs = A.T @ (lam[0].ravel() * y[0].ravel()) + v.ravel() / sigma ** 2
+    exact = np.linalg.solve(H, rhs)
+    z = oracle.prox_data_frame(y[0], lam[0], v, z0, sc, ang, sigma, 64)
+    np.testing.assert_allclose(z.ravel(), exact, rtol=1e-8, atol=1e-10)
+
+
+def test_cg_energy_error_decreases(oracle):
+    # CG minimises the H-norm of the error over growing Krylov spaces, so that
+    # norm cannot increase from one iteration count to the next.
+    sc, y, lam = _tiny_problem(oracle, seed=3)
+    ang = sc.angles()[0]
+    shape = (4, 4, 4)
+    A = _dense_A(oracle, sc, ang, shape)
+    sigma = 1.0
+    v = synth.normal(4, shape)
+    H = A.T @ (lam[0].ravel()[:, None] * A) + np.eye(64) / sigma ** 2
+    exact = np.linalg.solve(H, A.T @ (lam[0].ravel() * y[0].ravel()) + v.ravel() / sigma ** 2)
+    prev = math.inf
+    for k in range(0, 12):
+        e = oracle.prox_data_frame(y[0], lam[0], v, np.zeros(shape), sc, ang, sigma, k).ravel() - exact
+        en = float(e @ H @ e)
+        assert en <= prev * (1 + 1e-12)
+        prev = en
+
+
+def _gmrf_Q(shape4, sx, bt):
+    # Hessian of h(z) = sum_{pairs} b rho(z_s - z_r) with p = q = 2, where
+    # rho(D) = D^2/(4 sx^2): each pair adds b/(2 sx^2) [[1,-1],[-1,1]].
+    nt, nz, ny, nx = shape4
+    N = nt * nz * ny * nx
+    Q = np.zeros((N, N))
+    s = 6 + 12 / math.sqrt(2) + 8 / math.sqrt(3)
+    idx = np.arange(N).reshape(shape4)
+    for t in range(nt):
+        for z in range(nz):
+            for yy in range(ny):
+                for x in range(nx):
+                    i = idx[t, z, yy, x]
+                    for dz in (-1, 0, 1):
+                        for dy in (-1, 0, 1):
+                            for dx in (-1, 0, 1):
+                                if (dz, dy, dx) == (0, 0, 0):
+                                    continue
+                                z2, y2, x2 = z + dz, yy + dy, x + dx
+                                if not (0 <= z2 < nz and 0 <= y2 < ny and 0 <= x2 < nx):
+                                    continue
+                                b = 1.0 / (math.sqrt(abs(dz) + abs(dy) + abs(dx)) * s)
+                                j = idx[t, z2, y2, x2]
+                                c = b / (2 * sx ** 2) / 2  # each ordered pair visited twice
+                                Q[i, i] += c; Q[j, j] += c; Q[i, j] -= c; Q[j, i] -= c
+                    if t + 1 < nt:
+                        j = idx[t + 1, z, yy, x]
+                        c = bt / (2 * sx ** 2)
+                        Q[i, i] += c; Q[j, j] += c; Q[i, j] -= c; Q[j, i] -= c
+    return Q
+
+
+def test_qggmrf_quadratic_case_equals_linear_solve(oracle):
+    # p = q = 2 makes the q-GGMRF a Gaussian MRF: H(v) = (I/sigma^2 + Q)^-1 v/sigma^2.
+    shape = (3, 3, 4, 3)
+    v = synth.normal(5, shape)
+    sigma, sx, bt = 0.7, 0.5, 0.5
+    Q = _gmrf_Q(shape, sx, bt)
+    exact = np.linalg.solve(np.eye(v.size) / sigma ** 2 + Q, v.ravel() / sigma ** 2)
+    z = oracle.prox_qggmrf(v, np.zeros(shape), sigma, 2.0, 2.0, 1.0, sx, bt, 400)
+    np.testing.assert_allclose(z.ravel(), exact, rtol=1e-9, atol=1e-11)
+    # the cost function agrees with the quadratic form
+    assert oracle.qggmrf_cost(z, 2.0, 2.0, 1.0, sx, bt) == pytest.approx(0.5 * z.ravel() @ Q @ z.ravel(), rel=1e-12)
+
+
+def test_qggmrf_potential_and_surrogate(oracle):
+    p, q, T, sx = 2.0, 1.2, 1.0, 0.3
+    # rho ~ D^2/(2 sx^2) near 0 and ~ |D|^q (T sx)^(p-q)/(p sx^p) for large |D|
+    d = 1e-6
+    assert oracle.qggmrf_rho(d, p, q, T, sx) == pytest.approx(d * d / (2 * sx * sx), rel=1e-4)
+    d = 1e6
+    assert oracle.qggmrf_rho(d, p, q, T, sx) == pytest.approx(d ** q * (T * sx) ** (p - q) / (p * sx ** p), rel=1e-4)
+    # a(D) = rho'(D) / (2 D), with rho' from central differences
+    for d in (-2.0, -0.3, 0.01, 0.2, 1.7):
+        h = 1e-6 * max(1.0, abs(d))
+        drho = (oracle.qggmrf_rho(d + h, p, q, T, sx) - oracle.qggmrf_rho(d - h, p, q, T, sx)) / (2 * h)
+        assert oracle.qggmrf_coef(d, p, q, T, sx) == pytest.approx(drho / (2 * d), rel=1e-6)
+    assert oracle.qggmrf_coef(0.0, p, q, T, sx) == pytest.approx(1.0 / (2 * sx * sx), rel=1e-15)
+
+
+def test_qggmrf_icd_reaches_stationary_point(oracle):
+    # Converged ICD satisfies the first-order condition of Eq. (5):
+    # (z - v)/sigma^2 + grad h(z) = 0, with grad h from differences of the cost.
+    shape = (2, 3, 3, 3)
+    v = synth.uniform(6, shape, 0.0, 2.0)
+    sigma, p, q, T, sx, bt = 0.5, 2.0, 1.2, 1.0, 0.4, 0.5
+    z = oracle.prox_qggmrf(v, v.copy(), sigma, p, q, T, sx, bt, 3000)
+    g = np.zeros(z.size)
+    zf = z.ravel()
+    for i in range(z.size):
+        h = 1e-6
+        zp = zf.copy(); zp[i] += h
+        zm = zf.copy(); zm[i] -= h
+        g[i] = (oracle.qggmrf_cost(zp.reshape(shape), p, q, T, sx, bt)
+                - oracle.qggmrf_cost(zm.reshape(shape), p, q, T, sx, bt)) / (2 * h)
+    kkt = (zf - v.ravel()) / sigma ** 2 + g
+    assert np.abs(kkt).max() < 1e-6 * np.abs(v.ravel() / sigma ** 2).max()
+
+
+def test_qggmrf_icd_is_monotone(oracle):
+    # Each ICD update minimises a majoriser of the prox cost, so the cost never rises.
+    shape = (3, 4, 4, 4)
+    v = synth.uniform(7, shape, 0.0, 2.0)
+    sigma, p, q, T, sx, bt = 0.2, 2.0, 1.2, 1.0, 0.1, 0.5
+    z = np.zeros(shape)
+    cost = lambda z: float(((z - v) ** 2).sum() / (2 * sigma ** 2)) + oracle.qggmrf_cost(z, p, q, T, sx, bt)
+    prev = cost(z)
+    for _ in range(6):
+        z = oracle.prox_qggmrf(v, z, sigma, p, q, T, sx, bt, 1)
+        c = cost(z)
+        assert c <= prev + 1e-12
+        prev = c
+
+
+def test_G_involution_and_mann_forms(oracle):
+    # (2G - I)(2G - I) = I (Sec. III) and Algorithm 1 equals the Mann update of Eq. (12).
+    rng = np.random.default_rng(8)
+    K = 3
+    mu = oracle.mu_from_beta(3.0, K)
+    assert mu.sum() == pytest.approx(1.0) and np.allclose(mu, 0.25)
+    W = [rng.standard_normal((2, 3, 4)) for _ in range(K + 1)]
+    V = [2 * g - w for g, w in zip(oracle.G(W, mu), W)]
+    VV = [2 * g - v for g, v in zip(oracle.G(V, mu), V)]
+    for a, b in zip(VV, W):
+        np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-13)
+    mats = [rng.standard_normal((24, 24)) * 0.3 for _ in range(K + 1)]
+    agents = [lambda w, x, M=M: (M @ w.ravel()).reshape(w.shape) for M in mats]
+    X = [np.zeros_like(w) for w in W]
+    rho = 0.8
+    W1, X1, _ = oracle.mace_iteration(W, X, agents, mu, rho)
+    W2 = oracle.mann_step_direct(W, [a(w, None) for a, w in zip(agents, W)], mu, rho)
+    for a, b in zip(W1, W2):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_mace_fixed_point_is_map_solution(oracle):
+    # With proximal agents, the consensus solves Eq. (3):
+    # (A^T Lambda A + (beta/K) sum_k Q_k) x = A^T Lambda y.  Agents here: the
+    # oracle's CG prox (run to convergence) and two quadratic-MRF ICD proxes.
+    n, nt = 4, 2
+    sc, y, lam = _tiny_problem(oracle, n=n, nt=nt, seed=9)
+    shape4 = (nt, n, n, n)
+    sigma, beta, K = 0.5, 1.0, 2
+    mu = oracle.mu_from_beta(beta, K)
+    prm = [(0.6, 0.5), (0.3, 1.0)]  # (sigma_x, b_temporal) of the two priors
+    agents = [lambda w, x: oracle.prox_data(y, lam, w, x, sc, sigma, 64)]
+    for sx, bt in prm:
+        agents.append(lambda w, x, sx=sx, bt=bt: oracle.prox_qggmrf(w, x, sigma, 2.0, 2.0, 1.0, sx, bt, 300))
+    x0 = np.zeros(shape4)
+    xhat, W, X, res = oracle.mace(x0, agents, mu, 0.5, 150)
+    ang = sc.angles()
+    N3 = n ** 3
+    H = np.zeros((nt * N3, nt * N3))
+    b = np.zeros(nt * N3)
+    for t in range(nt):
+        A = _dense_A(oracle, sc, ang[t], (n, n, n))
+        H[t * N3:(t + 1) * N3, t * N3:(t + 1) * N3] = A.T @ (lam[t].ravel()[:, None] * A)
+        b[t * N3:(t + 1) * N3] = A.T @ (lam[t].ravel() * y[t].ravel())
+    for sx, bt in prm:
+        H += beta / K * _gmrf_Q(shape4, sx, bt)
+    exact = np.linalg.solve(H, b)
+    np.testing.assert_allclose(xhat.ravel(), exact, rtol=1e-7, atol=1e-9 * np.abs(exact).max())
+    np.testing.assert_allclose(oracle.average(X, mu).ravel(), exact, rtol=1e-7, atol=1e-9 * np.abs(exact).max())
+    assert res[-1] < 1e-7 < res[0]
