@@ -1,0 +1,262 @@
+/*
+ * msf.h -- C ABI of the GB300 multi-slice fusion library (libmsf.so).
+ *
+ * Method: "Multi-Slice Fusion for Sparse-View and Limited-Angle 4D CT
+ * Reconstruction" (arXiv 2008.01567).  One Mann iteration of multi-agent
+ * consensus equilibrium (MACE) on a 4D (x,y,z,t) volume: a per-frame data
+ * proximal map L (Sec. III, Eq. (4)) built on a cone-beam projector A_n
+ * (Sec. II, Eq. (2)), K prior agents H_k (Eq. (5)) -- three 2.5D CNN denoisers
+ * (Sec. IV, Eq. (14)) or a 4D q-GGMRF MRF prior (Sec. VII) -- and the consensus
+ * update of Algorithm 1.
+ *
+ * Conventions (every entry point):
+ *  - Pointers named d_* are device pointers owned by the caller; h_* are host
+ *    pointers.  The library never frees caller memory.  Handles own only their
+ *    geometry tables, weights and workspaces, all allocated in *_create.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream).  Functions that return a host value (h_loss, h_residual)
+ *    synchronise that stream before returning.
+ *  - Return MSF_OK or an error code; nothing is thrown across the ABI.
+ *    Argument errors are detected before any launch.  msf_last_error() gives a
+ *    thread-local description of the last failure in the calling thread.
+ *  - Layouts: a 3D frame is [nz][ny][nx] (x fastest); a 4D volume is
+ *    [nt][nz][ny][nx]; a sinogram is [nt][views][nv][nu] (u fastest); a stack of
+ *    K+1 agent states is [K+1][nt][nz][ny][nx].  All float data is FP32.
+ *  - Geometry: voxel (ix,iy,iz) has centre ((ix-(nx-1)/2)*voxel, ...), the
+ *    rotation axis is z, view angle th puts the source at
+ *    (dso cos th, dso sin th, 0) and the detector centre at
+ *    -(dsd-dso)(cos th, sin th, 0), with u axis (-sin th, cos th, 0) and v axis
+ *    (0,0,1); pixel (iu,iv) sits at (iu-(nu-1)/2)*du, (iv-(nv-1)/2)*dv.
+ */
+#ifndef MSF_H
+#define MSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MSF_OK = 0,
+    MSF_ERR_ARG = 1,        /* invalid argument; nothing was launched */
+    MSF_ERR_CUDA = 2,       /* a CUDA runtime/driver call failed */
+    MSF_ERR_NOMEM = 3,      /* device allocation failed in a *_create call */
+    MSF_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
+    MSF_ERR_NUMERIC = 5,    /* non-finite value detected in a reduction */
+    MSF_ERR_UNSUPPORTED = 6 /* device is not sm_103 / feature not built */
+} msf_status;
+
+/* Thread-local message for the last non-OK status returned in this thread. */
+const char* msf_last_error(void);
+/* Library version string. */
+const char* msf_version(void);
+
+/* Per-kernel timing (diagnostics, off by default).  While enabled, every kernel
+ * launch of the library is bracketed by a CUDA event pair recorded on the
+ * launch's stream.  msf_profile_read synchronises the recorded events and
+ * returns the number of distinct kernel names seen since the last reset; for
+ * entry i < that number it fills *name (static string), *launches and
+ * *total_ms (sum of the launches' event-measured durations).  Not for use
+ * while a stream is being captured into a CUDA graph. */
+void msf_profile_enable(int on);
+void msf_profile_reset(void);
+int msf_profile_read(int i, const char** name, int64_t* launches, double* total_ms);
+
+/* ------------------------------------------------------------ problem data */
+
+/* One 4D volume: nt frames of nx*ny*nz isotropic voxels of edge `voxel`
+ * (the x_n of Sec. II: N = nt * Ns, Ns = nx*ny*nz). */
+typedef struct {
+    int nx, ny, nz, nt;
+    double voxel;
+} msf_vol;
+
+/* Circular-orbit flat-detector cone-beam scan (the measurement model of
+ * Sec. II; the projection geometry is this library's reading, see msf.h head).
+ * `views` views per time-point; angles[t*views + j] in radians (host memory,
+ * copied at msf_projector_create). */
+typedef struct {
+    int nu, nv, views;
+    double du, dv;
+    double dso, dsd;
+    const double* angles;
+} msf_geom;
+
+/* ------------------------------------------------------------ projector */
+
+typedef struct msf_projector msf_projector;
+
+/* Builds the projector plan for (geom, vol): a per-(view, detector column)
+ * table of ray constants computed in FP64 on the device and stored in FP32.
+ * Errors: MSF_ERR_ARG when sizes are non-positive, when the source or detector
+ * would lie inside the volume's circumscribed cylinder (dso and dsd-dso must
+ * exceed its radius), or when a ray could be steeper than 45 deg to the
+ * rotation plane (the z-major case, which this projector does not model).
+ * Allocates the table plus one transposed frame stack (4*N bytes). */
+msf_status msf_projector_create(const msf_geom* geom, const msf_vol* vol, msf_projector** out);
+void msf_projector_destroy(msf_projector* p);
+/* Device bytes held by the plan. */
+size_t msf_projector_bytes(const msf_projector* p);
+
+/* y = A x for every time-point: the system matrix A_n of Sec. II, Eq. (2),
+ * modelled as a Joseph ray-driven projector.  For each ray (one per detector
+ * pixel and view) the major axis is x when |d_x| >= |d_y| else y; on every
+ * voxel-centre plane of that axis the frame is sampled bilinearly at the ray's
+ * crossing point (taps outside the volume are zero) and weighted by
+ * voxel*|d|/|d_major|.  d_x: [nt][nz][ny][nx]; d_y: [nt][views][nv][nu]
+ * (overwritten).  FP32 arithmetic; per-ray constants from the FP64 plan. */
+msf_status msf_project(msf_projector* p, const float* d_x, float* d_y, void* stream);
+
+/* x = A^T y for every time-point: the matched adjoint of msf_project, computed
+ * as a voxel-driven gather (no atomics) that re-derives, bit for bit, the
+ * forward's interpolation weights for every ray touching the voxel.
+ * d_y: sinogram; d_x: 4D volume (overwritten). */
+msf_status msf_backproject(msf_projector* p, const float* d_y, float* d_x, void* stream);
+
+/* Measurement conditioning for M = nt*views*nv*nu rays:
+ *   y = -ln(max(n,1)/I0)                (log-normalised counts)
+ *   Lambda = c exp(-y)                   (Sec. II, the diagonal weight Lambda_n)
+ * d_counts: photon counts; d_y, d_lambda: outputs (either may be NULL). */
+msf_status msf_weights(const float* d_counts, float* d_y, float* d_lambda, size_t m,
+                       double I0, double c, void* stream);
+
+/* ------------------------------------------------------------ data agent */
+
+typedef struct msf_dataprox msf_dataprox;
+
+/* Workspace for the data proximal map on the projector's problem size:
+ * four 4D volumes, one sinogram and per-frame FP64 scalars. */
+msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out);
+void msf_dataprox_destroy(msf_dataprox* d);
+
+/* Partial-update data proximal map L~(v; x) of Sec. III, Eq. (13): n_cg
+ * conjugate-gradient iterations on
+ *     (A^T Lambda A + I/sigma^2) z = A^T Lambda y + v/sigma^2
+ * (the minimiser of Eq. (4) with l from Eq. (2)), one independent solve per
+ * time-point, warm-started from d_x and written back to d_x.  Vectors are FP32;
+ * the dot products and the step scalars alpha, beta are FP64 per frame.
+ * d_y, d_lambda: sinogram-shaped; d_v, d_x: 4D volumes.  sigma > 0, n_cg >= 0. */
+msf_status msf_prox_data(msf_dataprox* d, const float* d_y, const float* d_lambda,
+                         const float* d_v, float* d_x, double sigma, int n_cg, void* stream);
+
+/* ------------------------------------------------------------ q-GGMRF agent */
+
+/* 4D q-GGMRF MRF prior (Sec. VII, "MBIR+4D-MRF"): 26 spatial neighbours with
+ * weights proportional to 1/distance normalised to sum 1, plus the two temporal
+ * neighbours with weight b_temporal each; free boundaries.  Potential
+ * rho(D) = |D|^p/(p sx^p) * u/(1+u), u = |D/(T sx)|^(q-p).  p must be 2 and
+ * 1 <= q <= 2 (the symmetric-bound surrogate is then finite everywhere). */
+typedef struct {
+    double p, q, T, sigma_x, b_temporal;
+} msf_mrf;
+
+/* Prior proximal map H(v) of Sec. III, Eq. (5) for the q-GGMRF prior:
+ * n_sweeps ICD sweeps in place on d_x (its content is the starting point).
+ * A sweep visits the 16 parity colours ((pt*2+pz)*2+py)*2+px in increasing
+ * order; each voxel takes the minimiser of the symmetric-bound surrogate
+ *   z_s = (v_s/sigma^2 + 2 sum_r b_sr a(z_s-z_r) z_r) / (1/sigma^2 + 2 sum_r b_sr a(z_s-z_r)).
+ * d_v, d_x: 4D volumes [nt][nz][ny][nx]. */
+msf_status msf_prox_qggmrf(const msf_vol* vol, const msf_mrf* prm, const float* d_v, float* d_x,
+                           double sigma, int n_sweeps, void* stream);
+
+/* ------------------------------------------------------------ CNN agents */
+
+/* Agent orientation (Sec. IV): convolution plane and slicing axis.
+ * XY_T: slices z, image rows y, cols x.  YZ_T: slices x, rows z, cols y.
+ * ZX_T: slices y, rows x, cols z.  Channels: time-points t-2..t+2 of the same
+ * slice, clamped at the first and last time-point. */
+typedef enum { MSF_XY_T = 0, MSF_YZ_T = 1, MSF_ZX_T = 2 } msf_orient;
+
+typedef struct msf_cnn msf_cnn;
+
+/* The 2.5D residual CNN of Sec. IV: layer 1 conv 5->64 + bias + ReLU; layers
+ * 2..9 conv 64->64 + BatchNorm + ReLU; layer 10 conv 64->1 + bias; output
+ * = centre frame - network output (residual through the centre channel).
+ * 3x3 kernels, zero padding.  Inference runs BF16 tcgen05 implicit-GEMM
+ * convolutions with FP32 accumulation and BatchNorm folded into the weights.
+ * max_pixels bounds the images * H * W processed per internal chunk
+ * (activation workspace = 2 * max_pixels * 128 bytes). */
+msf_status msf_cnn_create(int64_t max_pixels, msf_cnn** out);
+void msf_cnn_destroy(msf_cnn* c);
+
+/* Number of FP32 parameters in the flat host layout used by set/get:
+ * for l = 1..10: W_l [Cout][Cin][3][3] then b_l [Cout]; then for l = 2..9:
+ * gamma_l[64], beta_l[64], running_mean_l[64], running_var_l[64]. */
+size_t msf_cnn_param_count(void);
+msf_status msf_cnn_set_params(msf_cnn* c, const float* h_params, size_t n);
+msf_status msf_cnn_get_params(msf_cnn* c, float* h_params, size_t n);
+
+/* Agent H_{orient,t}: d_in, d_out are 4D volumes described by vol.
+ * Each output voxel = centre - CNN(5-frame window), computed slice by slice. */
+msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* vol,
+                       const float* d_in, float* d_out, void* stream);
+
+/* One training step (Sec. V): forward with BatchNorm batch statistics, MSE loss
+ * mean((out - clean)^2), backward, and Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+ * bias-corrected) on FP32 master weights; running BatchNorm statistics are
+ * updated with momentum 0.1.  d_noisy: [B][5][H][W], d_clean: [B][H][W].
+ * h_loss (optional) receives the loss of this step (synchronises). */
+msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const float* d_clean,
+                          int B, int H, int W, float lr, float* h_loss, void* stream);
+
+/* ------------------------------------------------------------ MACE */
+
+typedef enum { MSF_PRIOR_QGGMRF = 0, MSF_PRIOR_CNN = 1 } msf_prior_kind;
+
+typedef struct msf_mace msf_mace;
+
+/* A MACE problem.  K prior agents: with MSF_PRIOR_CNN, K = 3 and the agents
+ * are H_xy,t, H_yz,t, H_zx,t sharing `cnn` (Eq. (14)); with MSF_PRIOR_QGGMRF,
+ * K = 1 and the agent is the q-GGMRF prox with `mrf`.  d_W and d_X hold the
+ * K+1 stacked states [K+1][nt][nz][ny][nx] (caller-owned, initialised by the
+ * caller; Algorithm 1 starts from W = X = [x0; ...; x0]).  d_y, d_lambda: the
+ * measurements and weights.  The handle borrows proj and cnn. */
+typedef struct {
+    msf_projector* proj;
+    msf_prior_kind prior;
+    int K;
+    msf_cnn* cnn;
+    msf_mrf mrf;
+    float* d_W;
+    float* d_X;
+    const float* d_y;
+    const float* d_lambda;
+} msf_mace_desc;
+
+typedef struct {
+    double rho;       /* Mann weight, 0 < rho < 1 (Eq. (12)) */
+    double sigma;     /* proximal scale sigma > 0 (Eqs. (4)-(5)) */
+    double mu[4];     /* agent weights of the average, Eq. (9); sum to 1 */
+    int n_cg;         /* CG iterations of the partial update L~ (Eq. (13)) */
+    int n_sweeps;     /* ICD sweeps of the q-GGMRF agent per iteration */
+} msf_mace_params;
+
+msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out);
+void msf_mace_destroy(msf_mace* m);
+
+/* One pass of Algorithm 1:  X <- F~(W; X);  Z <- G(2X - W);  W <- W + 2 rho (Z - X).
+ * X_0 <- L~(W_0; X_0) (warm-started CG), X_k <- H_k(W_k); the average of Eq. (9)
+ * uses mu.  h_residual (optional, synchronises) receives the FP64 consensus
+ * spread sqrt(sum_i mu_i ||X_i - Xbar||^2) / ||Xbar|| of the new X. */
+msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, double* h_residual, void* stream);
+
+/* ------------------------------------------------------------ phantoms (test/bench data) */
+
+/* Ellipsoid phantom records, 16 doubles each (host): centre(3), semi-axes(3),
+ * rotation (9, row-major, row k = k-th axis), attenuation mu(1); overlaps add.
+ * ell[t*n_ell + e] describes ellipsoid e at time-point t. */
+
+/* Supersampled voxelisation: value = sum_e mu_e * fraction of the ss^3
+ * sub-voxel sample points inside e.  d_x: 4D volume. */
+msf_status msf_phantom_voxelize(const msf_vol* vol, const double* h_ell, int n_ell, int ss,
+                                float* d_x, void* stream);
+/* Exact line integrals of the phantom along every ray of the plan's scan. */
+msf_status msf_phantom_project(msf_projector* p, const double* h_ell, int n_ell,
+                               float* d_y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSF_H */

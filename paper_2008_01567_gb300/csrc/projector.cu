@@ -1,0 +1,753 @@
+// Cone-beam Joseph projector pair and the CG data proximal map.
+//
+// A_n (Sec. II, Eq. (2)) is modelled as a Joseph ray-driven projector on a
+// circular orbit with a flat detector (the paper defers the model to its
+// cone-beam reference; the geometry is documented in msf.h).  The adjoint is a
+// voxel-driven gather: each voxel enumerates the rays whose bilinear footprint
+// touches it and recomputes the forward's interpolation coordinates with the
+// same FP32 operations, so A^T is exactly the transpose of the FP32 A up to
+// summation order, without atomics.
+//
+// Per (view, detector column) constants are computed once in FP64 and stored
+// in FP32.  A ray's direction has d_x, d_y fixed by its column and d_z = v, so
+// the in-plane constants are per column and the z constants are v times
+// per-column factors.  Along the major axis the crossing point at plane k is
+//     f_a(k) = fa_mid + (k - c_maj) * ba          (minor in-plane axis)
+//     f_z(k) = (c_z + v*c1) + (k - c_maj) * (v*inv_dmaj)
+// in fractional voxel indices, and the chord per plane is
+//     step = sqrt(|d_xy|^2 + v^2) * voxel/|d_maj|.
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace msf {
+
+struct ColParams {
+    float fa_mid, ba, c1, inv_dmaj;   // minor-axis line, z factors
+    float dxy2, vox_over_adm, xmajor, pad;
+};
+
+struct ProjDims {
+    int nx, ny, nz, nt, nu, nv, views;
+    float cx, cy, cz, cu, cv;   // (n-1)/2 of each axis
+    float vox, du, dv;
+    float dso, dsd;
+};
+
+struct RayZ {
+    float fz_mid, bz, step;
+};
+
+// The one place where a ray's z constants are formed; forward and adjoint
+// both call it, with explicit round-to-nearest intrinsics so the compiler
+// cannot contract the two call sites differently.
+__device__ __forceinline__ RayZ ray_z(const ColParams& c, float v, float cz) {
+    RayZ r;
+    r.fz_mid = __fmaf_rn(v, c.c1, cz);
+    r.bz = __fmul_rn(v, c.inv_dmaj);
+    r.step = __fmul_rn(__fsqrt_rn(__fmaf_rn(v, v, c.dxy2)), c.vox_over_adm);
+    return r;
+}
+
+__device__ __forceinline__ float det_v(int iv, const ProjDims& d) {
+    return __fmul_rn(__fsub_rn((float)iv, d.cv), d.dv);
+}
+
+__device__ __forceinline__ ColParams load_col(const float4* __restrict__ col, size_t idx) {
+    float4 a = __ldg(col + 2 * idx), b = __ldg(col + 2 * idx + 1);
+    ColParams c;
+    c.fa_mid = a.x; c.ba = a.y; c.c1 = a.z; c.inv_dmaj = a.w;
+    c.dxy2 = b.x; c.vox_over_adm = b.y; c.xmajor = b.z; c.pad = b.w;
+    return c;
+}
+
+// ------------------------------------------------------------------ FP64 table
+
+// One thread per (frame-view g, column iu).  Writes the column constants and
+// flags geometry the model does not cover: a plane crossing outside the
+// source-detector segment (0 < lambda < 1) on the first or last plane.
+__global__ void column_table_kernel(const double* __restrict__ angles, float4* __restrict__ col,
+                                    int* __restrict__ bad, ProjDims d, double vox, double du,
+                                    double dso, double dsd) {
+    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    if (iu >= d.nu) return;
+    const double th = angles[g];
+    const double c = cos(th), s = sin(th);
+    const double u = (iu - 0.5 * (d.nu - 1)) * du;
+    const double sx = dso * c, sy = dso * s;
+    const double px = -(dsd - dso) * c - u * s;
+    const double py = -(dsd - dso) * s + u * c;
+    const double dx = px - sx, dy = py - sy;
+    const bool xmaj = fabs(dx) >= fabs(dy);
+    const double dmaj = xmaj ? dx : dy, smaj = xmaj ? sx : sy;
+    const double da = xmaj ? dy : dx, sa = xmaj ? sy : sx;
+    const int nmaj = xmaj ? d.nx : d.ny, na = xmaj ? d.ny : d.nx;
+    const double lam0 = -smaj / dmaj;
+    float4 a, b;
+    a.x = (float)((sa + lam0 * da) / vox + 0.5 * (na - 1));
+    a.y = (float)(da / dmaj);
+    a.z = (float)(lam0 / vox);
+    a.w = (float)(1.0 / dmaj);
+    b.x = (float)(dx * dx + dy * dy);
+    b.y = (float)(vox / fabs(dmaj));
+    b.z = xmaj ? 1.0f : 0.0f;
+    b.w = 0.0f;
+    const size_t idx = (size_t)g * d.nu + iu;
+    col[2 * idx] = a;
+    col[2 * idx + 1] = b;
+    const double lfirst = lam0 + (0 - 0.5 * (nmaj - 1)) * vox / dmaj;
+    const double llast = lam0 + (nmaj - 1 - 0.5 * (nmaj - 1)) * vox / dmaj;
+    if (!(fmin(lfirst, llast) > 0.0 && fmax(lfirst, llast) < 1.0)) atomicExch(bad, 1);
+    (void)na;
+}
+
+// ------------------------------------------------------------------ transpose
+
+// Per frame and z-slice: out[x][y] = in[y][x] (x-major rays read the frame with
+// y contiguous).  FUSED: p <- r + beta_t p, written back and transposed (the
+// CG direction update folded into the transpose of the next forward pass).
+template <bool FUSED>
+__global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                 const float* __restrict__ r, float* __restrict__ p,
+                                 const double* __restrict__ beta, int nx, int ny, int nz) {
+    __shared__ float tile[32][33];
+    const int slice = blockIdx.z;             // t * nz + z
+    const int t = slice / nz;
+    const size_t base = (size_t)slice * nx * ny;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    float bt = 0.0f;
+    if (FUSED) bt = (float)beta[t];
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int x = x0 + threadIdx.x, y = y0 + k;
+        if (x < nx && y < ny) {
+            const size_t i = base + (size_t)y * nx + x;
+            float val;
+            if (FUSED) {
+                val = __fmaf_rn(bt, p[i], r[i]);
+                p[i] = val;
+            } else {
+                val = in[i];
+            }
+            tile[k][threadIdx.x] = val;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int y = y0 + threadIdx.x, x = x0 + k;
+        if (x < nx && y < ny) out[base + (size_t)x * ny + y] = tile[threadIdx.x][k];
+    }
+}
+
+// ------------------------------------------------------------------ forward
+
+enum FwdMode { FWD_PLAIN = 0, FWD_LAMBDA = 1, FWD_RESIDUAL = 2 };
+
+// One thread per ray; block = 32 columns x 4 rows of one view.  x-major rays
+// read the transposed frame [nz][nx][ny], y-major rays the natural frame
+// [nz][ny][nx], so in both cases the minor in-plane axis is contiguous.
+//   FWD_PLAIN:    out = A x
+//   FWD_LAMBDA:   out = Lambda * (A x)
+//   FWD_RESIDUAL: out = Lambda * (meas - A x)
+template <int MODE>
+__global__ void __launch_bounds__(128) joseph_fwd_kernel(
+    const float* __restrict__ x, const float* __restrict__ xT, const float4* __restrict__ col,
+    float* __restrict__ out, const float* __restrict__ lam, const float* __restrict__ meas,
+    ProjDims d) {
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * 4 + threadIdx.y;
+    const int g = blockIdx.z;
+    if (iu >= d.nu || iv >= d.nv) return;
+    const int t = g / d.views;
+    const ColParams c = load_col(col, (size_t)g * d.nu + iu);
+    const bool xmaj = c.xmajor != 0.0f;
+    const int nmaj = xmaj ? d.nx : d.ny, na = xmaj ? d.ny : d.nx;
+    const size_t fs = (size_t)d.nx * d.ny * d.nz;
+    const float* __restrict__ vol = (xmaj ? xT : x) + (size_t)t * fs;
+    const float cmaj = xmaj ? d.cx : d.cy;
+    const RayZ rz = ray_z(c, det_v(iv, d), d.cz);
+
+    // planes where the crossing point can touch the grid: -1 < f < n on both
+    // minor axes; computed conservatively (one plane of margin each side)
+    float klo = 0.0f, khi = (float)(nmaj - 1);
+    {
+        const float fm[2] = {c.fa_mid, rz.fz_mid}, bb[2] = {c.ba, rz.bz};
+        const float hi[2] = {(float)na, (float)d.nz};
+        for (int a = 0; a < 2; ++a) {
+            if (fabsf(bb[a]) > 1e-12f) {
+                float k1 = (-1.0f - fm[a]) / bb[a] + cmaj, k2 = (hi[a] - fm[a]) / bb[a] + cmaj;
+                klo = fmaxf(klo, floorf(fminf(k1, k2)) - 1.0f);
+                khi = fminf(khi, ceilf(fmaxf(k1, k2)) + 1.0f);
+            } else if (!(fm[a] > -1.0f && fm[a] < hi[a])) {
+                khi = -1.0f;
+            }
+        }
+    }
+    float acc = 0.0f;
+    const int k0 = (int)klo, k1 = (int)khi;
+    for (int k = k0; k <= k1; ++k) {
+        const float tk = __fsub_rn((float)k, cmaj);
+        const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
+        const float fz = __fmaf_rn(tk, rz.bz, rz.fz_mid);
+        const float a0f = floorf(fa), z0f = floorf(fz);
+        const float wa1 = __fsub_rn(fa, a0f), wz1 = __fsub_rn(fz, z0f);
+        const int ia = (int)a0f, iz = (int)z0f;
+        const bool a_in0 = ia >= 0 && ia < na, a_in1 = ia + 1 >= 0 && ia + 1 < na;
+        const bool z_in0 = iz >= 0 && iz < d.nz, z_in1 = iz + 1 >= 0 && iz + 1 < d.nz;
+        const float* row0 = vol + ((ptrdiff_t)iz * nmaj + k) * na;
+        const float* row1 = row0 + (ptrdiff_t)nmaj * na;
+        const float v00 = (z_in0 && a_in0) ? __ldg(row0 + ia) : 0.0f;
+        const float v01 = (z_in0 && a_in1) ? __ldg(row0 + ia + 1) : 0.0f;
+        const float v10 = (z_in1 && a_in0) ? __ldg(row1 + ia) : 0.0f;
+        const float v11 = (z_in1 && a_in1) ? __ldg(row1 + ia + 1) : 0.0f;
+        const float wa0 = __fsub_rn(1.0f, wa1), wz0 = __fsub_rn(1.0f, wz1);
+        acc += wz0 * (wa0 * v00 + wa1 * v01) + wz1 * (wa0 * v10 + wa1 * v11);
+    }
+    const float val = acc * rz.step;
+    const size_t ray = ((size_t)g * d.nv + iv) * d.nu + iu;
+    if (MODE == FWD_PLAIN) out[ray] = val;
+    else if (MODE == FWD_LAMBDA) out[ray] = lam[ray] * val;
+    else out[ray] = lam[ray] * (meas[ray] - val);
+}
+
+// ------------------------------------------------------------------ adjoint (gather)
+
+enum AdjMode { ADJ_PLAIN = 0, ADJ_CG_INIT = 1, ADJ_CG_Q = 2 };
+
+// Detector u coordinate (in pixels) of the point (x, y, .) for view (cs, sn).
+__device__ __forceinline__ float u_pixel(float x, float y, float cs, float sn, const ProjDims& d) {
+    const float lat = -x * sn + y * cs;
+    const float depth = d.dso - x * cs - y * sn;
+    return d.dsd * lat / depth / d.du + d.cu;
+}
+
+// Sum over the rays of one view whose major axis is `XMAJ` of
+// w(ray, voxel) * e(ray).  For x-major rays the voxel is touched on plane
+// k = ix when floor(f_y) is iy-1 or iy; candidates are the detector columns
+// whose ray crosses that plane within one voxel of the centre in y (from the
+// exact projection of that segment, plus one column of margin), and on each
+// such column the rows whose f_z lies within one voxel of iz.
+template <bool XMAJ>
+__device__ __forceinline__ float gather_view(const float4* __restrict__ col,
+                                             const float* __restrict__ e, int g, int ix, int iy,
+                                             int iz, float cs, float sn, const ProjDims& d) {
+    const int kpl = XMAJ ? ix : iy;             // plane index along the major axis
+    const int ia = XMAJ ? iy : ix;              // voxel index on the minor axis
+    const float cmaj = XMAJ ? d.cx : d.cy;
+    const float xc = (ix - d.cx) * d.vox, yc = (iy - d.cy) * d.vox;
+    float u1, u2;
+    if (XMAJ) {
+        u1 = u_pixel(xc, yc - d.vox, cs, sn, d);
+        u2 = u_pixel(xc, yc + d.vox, cs, sn, d);
+    } else {
+        u1 = u_pixel(xc - d.vox, yc, cs, sn, d);
+        u2 = u_pixel(xc + d.vox, yc, cs, sn, d);
+    }
+    const int iu_lo = max(0, (int)floorf(fminf(u1, u2)) - 1);
+    const int iu_hi = min(d.nu - 1, (int)ceilf(fmaxf(u1, u2)) + 1);
+    const float tk = __fsub_rn((float)kpl, cmaj);
+    float acc = 0.0f;
+    for (int iu = iu_lo; iu <= iu_hi; ++iu) {
+        const ColParams c = load_col(col, (size_t)g * d.nu + iu);
+        if ((c.xmajor != 0.0f) != XMAJ) continue;
+        const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
+        const float a0f = floorf(fa);
+        const int a0 = (int)a0f;
+        if (ia != a0 && ia != a0 + 1) continue;
+        const float wa1 = __fsub_rn(fa, a0f);
+        const float wa = (ia == a0) ? __fsub_rn(1.0f, wa1) : wa1;
+        // f_z(v) = c_z + v (c1 + tk inv_dmaj): rows with f_z in (iz-1, iz+1)
+        const float gz = c.c1 + tk * c.inv_dmaj;
+        const float va = (iz - 1 - d.cz) / gz / d.dv + d.cv;
+        const float vb = (iz + 1 - d.cz) / gz / d.dv + d.cv;
+        const int iv_lo = max(0, (int)floorf(fminf(va, vb)) - 1);
+        const int iv_hi = min(d.nv - 1, (int)ceilf(fmaxf(va, vb)) + 1);
+        const float* erow = e + ((size_t)g * d.nv) * d.nu + iu;
+        for (int iv = iv_lo; iv <= iv_hi; ++iv) {
+            const RayZ rz = ray_z(c, det_v(iv, d), d.cz);
+            const float fz = __fmaf_rn(tk, rz.bz, rz.fz_mid);
+            const float z0f = floorf(fz);
+            const int z0 = (int)z0f;
+            if (iz != z0 && iz != z0 + 1) continue;
+            const float wz1 = __fsub_rn(fz, z0f);
+            const float wz = (iz == z0) ? __fsub_rn(1.0f, wz1) : wz1;
+            acc += rz.step * (wa * wz) * __ldg(erow + (size_t)iv * d.nu);
+        }
+    }
+    return acc;
+}
+
+// One thread per voxel; block 32 (x) x 4 (y) of one z-row pair.
+//   ADJ_PLAIN:   out = A^T e
+//   ADJ_CG_INIT: r = A^T e + (v - z)/sigma^2, p = r, partial sum r.r
+//   ADJ_CG_Q:    q = A^T e + p/sigma^2, partial sum p.q
+template <int MODE>
+__global__ void __launch_bounds__(128) joseph_adj_kernel(
+    const float4* __restrict__ col, const float2* __restrict__ trig, const float* __restrict__ e,
+    float* __restrict__ out, const float* __restrict__ a1, const float* __restrict__ a2,
+    float* __restrict__ out2, double* __restrict__ partial, float inv_s2, ProjDims d) {
+    const int ix = blockIdx.x * 32 + threadIdx.x;
+    const int iy = blockIdx.y * 4 + threadIdx.y;
+    const int iz = blockIdx.z % d.nz;
+    const int t = blockIdx.z / d.nz;
+    const bool inside = ix < d.nx && iy < d.ny;
+    float acc = 0.0f;
+    if (inside) {
+        for (int j = 0; j < d.views; ++j) {
+            const int g = t * d.views + j;
+            const float2 cs = __ldg(trig + g);
+            acc += gather_view<true>(col, e, g, ix, iy, iz, cs.x, cs.y, d);
+            acc += gather_view<false>(col, e, g, ix, iy, iz, cs.x, cs.y, d);
+        }
+    }
+    const size_t i = (((size_t)t * d.nz + iz) * d.ny + iy) * d.nx + ix;
+    double dot = 0.0;
+    if (MODE == ADJ_PLAIN) {
+        if (inside) out[i] = acc;
+    } else if (MODE == ADJ_CG_INIT) {
+        // a1 = v, a2 = z
+        if (inside) {
+            const float r = acc + (a1[i] - a2[i]) * inv_s2;
+            out[i] = r;
+            out2[i] = r;
+            dot = (double)r * (double)r;
+        }
+    } else {
+        // a1 = p
+        if (inside) {
+            const float p = a1[i];
+            const float q = acc + p * inv_s2;
+            out[i] = q;
+            dot = (double)p * (double)q;
+        }
+    }
+    if (MODE != ADJ_PLAIN) {
+        const double s = block_sum_f64(dot);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const int bpf = gridDim.x * gridDim.y * d.nz;   // blocks per frame
+            const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * iz);
+            partial[(size_t)t * bpf + b] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ CG scalars
+
+enum FinMode { FIN_RR0 = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+
+// One block per frame: sums that frame's block partials in a fixed order.
+//   FIN_RR0:   rr = sum
+//   FIN_ALPHA: alpha = rr / sum (0 when sum == 0)
+//   FIN_BETA:  beta = sum / rr (0 when rr == 0); rr = sum
+// Any non-finite sum raises the status flag.
+template <int MODE>
+__global__ void cg_finalize_kernel(const double* __restrict__ partial, int nparts,
+                                   double* __restrict__ rr, double* __restrict__ coef,
+                                   int* __restrict__ status) {
+    const int t = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[(size_t)t * nparts + i];
+    s = block_sum_f64(s);
+    if (threadIdx.x == 0) {
+        if (!isfinite(s)) atomicExch(status, (int)MSF_ERR_NUMERIC);
+        if (MODE == FIN_RR0) {
+            rr[t] = s;
+        } else if (MODE == FIN_ALPHA) {
+            coef[t] = (s != 0.0) ? rr[t] / s : 0.0;
+        } else {
+            coef[t] = (rr[t] != 0.0) ? s / rr[t] : 0.0;
+            rr[t] = s;
+        }
+    }
+}
+
+// z += alpha p; r -= alpha q; partial r.r  (grid: blocks_per_frame x nt)
+__global__ void cg_update_kernel(float* __restrict__ z, float* __restrict__ r,
+                                 const float* __restrict__ p, const float* __restrict__ q,
+                                 const double* __restrict__ alpha, double* __restrict__ partial,
+                                 size_t fs) {
+    const int t = blockIdx.y;
+    const float a = (float)alpha[t];
+    const size_t off = (size_t)t * fs;
+    double dot = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < fs;
+         i += (size_t)gridDim.x * blockDim.x) {
+        z[off + i] = __fmaf_rn(a, p[off + i], z[off + i]);
+        const float rn = __fmaf_rn(-a, q[off + i], r[off + i]);
+        r[off + i] = rn;
+        dot += (double)rn * (double)rn;
+    }
+    const double s = block_sum_f64(dot);
+    if (threadIdx.x == 0) partial[(size_t)t * gridDim.x + blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------------ phantom (test data)
+
+#define MSF_MAX_ELL_RECORDS 256
+__constant__ double c_ell[MSF_MAX_ELL_RECORDS * 16];
+
+__device__ __forceinline__ void ell_local(const double* e, double px, double py, double pz,
+                                          double* q) {
+    const double tx = px - e[0], ty = py - e[1], tz = pz - e[2];
+    for (int k = 0; k < 3; ++k)
+        q[k] = (e[6 + 3 * k] * tx + e[7 + 3 * k] * ty + e[8 + 3 * k] * tz) / e[3 + k];
+}
+
+__global__ void phantom_voxelize_kernel(float* __restrict__ x, int nx, int ny, int nz, int nt,
+                                        double vox, int n_ell, int ss) {
+    const size_t fs = (size_t)nx * ny * nz;
+    const size_t total = fs * nt;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int t = (int)(i / fs);
+        size_t r = i % fs;
+        const int iz = (int)(r / ((size_t)nx * ny));
+        r %= (size_t)nx * ny;
+        const int iy = (int)(r / nx), ix = (int)(r % nx);
+        double acc = 0.0;
+        for (int e = 0; e < n_ell; ++e) {
+            const double* E = c_ell + 16 * ((size_t)t * n_ell + e);
+            int inside = 0;
+            for (int a = 0; a < ss; ++a)
+                for (int b = 0; b < ss; ++b)
+                    for (int cc = 0; cc < ss; ++cc) {
+                        double q[3];
+                        ell_local(E, (ix - 0.5 * (nx - 1) + (cc + 0.5) / ss - 0.5) * vox,
+                                  (iy - 0.5 * (ny - 1) + (b + 0.5) / ss - 0.5) * vox,
+                                  (iz - 0.5 * (nz - 1) + (a + 0.5) / ss - 0.5) * vox, q);
+                        inside += (q[0] * q[0] + q[1] * q[1] + q[2] * q[2] <= 1.0);
+                    }
+            acc += E[15] * (double)inside / (double)(ss * ss * ss);
+        }
+        x[i] = (float)acc;
+    }
+}
+
+__global__ void phantom_project_kernel(const double* __restrict__ angles, float* __restrict__ y,
+                                       ProjDims d, double du, double dv, double dso, double dsd,
+                                       int n_ell) {
+    const size_t per_view = (size_t)d.nu * d.nv;
+    const size_t total = per_view * d.views * d.nt;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i / per_view);
+        const int t = g / d.views;
+        const int iv = (int)((i % per_view) / d.nu), iu = (int)(i % d.nu);
+        const double th = angles[g], c = cos(th), s = sin(th);
+        const double u = (iu - 0.5 * (d.nu - 1)) * du, v = (iv - 0.5 * (d.nv - 1)) * dv;
+        const double sx = dso * c, sy = dso * s;
+        const double dx = -(dsd - dso) * c - u * s - sx, dy = -(dsd - dso) * s + u * c - sy,
+                     dz = v;
+        const double len = sqrt(dx * dx + dy * dy + dz * dz);
+        double acc = 0.0;
+        for (int e = 0; e < n_ell; ++e) {
+            const double* E = c_ell + 16 * ((size_t)t * n_ell + e);
+            double q0[3], q1[3];
+            ell_local(E, sx, sy, 0.0, q0);
+            for (int k = 0; k < 3; ++k)
+                q1[k] = (E[6 + 3 * k] * dx + E[7 + 3 * k] * dy + E[8 + 3 * k] * dz) / E[3 + k];
+            const double A = q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2];
+            const double B = 2.0 * (q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2]);
+            const double C = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2] - 1.0;
+            const double disc = B * B - 4.0 * A * C;
+            if (disc > 0.0) acc += E[15] * len * sqrt(disc) / A;
+        }
+        y[i] = (float)acc;
+    }
+}
+
+}  // namespace msf
+
+// ====================================================================== handles
+
+struct msf_projector {
+    msf_geom geom;
+    msf_vol vol;
+    msf::ProjDims dims;
+    std::vector<double> angles;
+    double* d_angles = nullptr;
+    float4* d_col = nullptr;
+    float2* d_trig = nullptr;
+    float* d_xT = nullptr;
+    size_t bytes = 0;
+};
+
+struct msf_dataprox {
+    msf_projector* p = nullptr;
+    float *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_s = nullptr;
+    double *d_partial = nullptr, *d_rr = nullptr, *d_alpha = nullptr, *d_beta = nullptr;
+    int* d_status = nullptr;
+    int parts_adj = 0, parts_upd = 0, parts_max = 0;
+};
+
+namespace msf {
+
+static size_t frame_size(const msf_vol& v) { return (size_t)v.nx * v.ny * v.nz; }
+static size_t vol_size(const msf_vol& v) { return frame_size(v) * v.nt; }
+static size_t sino_size(const msf_projector* p) {
+    return (size_t)p->geom.nu * p->geom.nv * p->geom.views * p->vol.nt;
+}
+
+static msf_status launch_transpose(msf_projector* p, const float* in, float* out, cudaStream_t st) {
+    const msf_vol& v = p->vol;
+    dim3 grid((v.nx + 31) / 32, (v.ny + 31) / 32, v.nz * v.nt);
+    MSF_PROF("transpose", st);
+    transpose_kernel<false><<<grid, dim3(32, 8), 0, st>>>(in, out, nullptr, nullptr, nullptr, v.nx,
+                                                          v.ny, v.nz);
+    MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
+static msf_status launch_fwd(msf_projector* p, int mode, const float* x, float* out,
+                             const float* lam, const float* meas, cudaStream_t st) {
+    MSF_TRY(launch_transpose(p, x, p->d_xT, st));
+    const ProjDims& d = p->dims;
+    dim3 grid((d.nu + 31) / 32, (d.nv + 3) / 4, d.nt * d.views);
+    dim3 block(32, 4);
+    MSF_PROF("joseph_fwd", st);
+    if (mode == FWD_PLAIN)
+        joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
+    else if (mode == FWD_LAMBDA)
+        joseph_fwd_kernel<FWD_LAMBDA><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
+    else
+        joseph_fwd_kernel<FWD_RESIDUAL><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
+    MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
+static dim3 adj_grid(const ProjDims& d) { return dim3((d.nx + 31) / 32, (d.ny + 3) / 4, d.nz * d.nt); }
+
+static msf_status launch_adj(msf_projector* p, int mode, const float* e, float* out,
+                             const float* a1, const float* a2, float* out2, double* partial,
+                             float inv_s2, cudaStream_t st) {
+    const ProjDims& d = p->dims;
+    dim3 grid = adj_grid(d), block(32, 4);
+    MSF_PROF("joseph_adj", st);
+    if (mode == ADJ_PLAIN)
+        joseph_adj_kernel<ADJ_PLAIN><<<grid, block, 0, st>>>(p->d_col, p->d_trig, e, out, a1, a2, out2, partial, inv_s2, d);
+    else if (mode == ADJ_CG_INIT)
+        joseph_adj_kernel<ADJ_CG_INIT><<<grid, block, 0, st>>>(p->d_col, p->d_trig, e, out, a1, a2, out2, partial, inv_s2, d);
+    else
+        joseph_adj_kernel<ADJ_CG_Q><<<grid, block, 0, st>>>(p->d_col, p->d_trig, e, out, a1, a2, out2, partial, inv_s2, d);
+    MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
+}  // namespace msf
+
+using namespace msf;
+
+const msf_vol* msf::projector_volume(const msf_projector* p) { return &p->vol; }
+
+extern "C" msf_status msf_projector_create(const msf_geom* geom, const msf_vol* vol,
+                                           msf_projector** out) {
+    MSF_REQUIRE(geom && vol && out, "msf_projector_create: NULL argument");
+    *out = nullptr;
+    MSF_REQUIRE(vol->nx > 0 && vol->ny > 0 && vol->nz > 0 && vol->nt > 0 && vol->voxel > 0,
+                "msf_projector_create: volume sizes and voxel must be positive");
+    MSF_REQUIRE(geom->nu > 0 && geom->nv > 0 && geom->views > 0 && geom->du > 0 && geom->dv > 0,
+                "msf_projector_create: detector sizes, pitch and views must be positive");
+    MSF_REQUIRE(geom->angles != nullptr, "msf_projector_create: angles is NULL");
+    const double R = 0.5 * vol->voxel * sqrt((double)vol->nx * vol->nx + (double)vol->ny * vol->ny);
+    MSF_REQUIRE(geom->dso > R && geom->dsd - geom->dso > R,
+                "msf_projector_create: source (dso=%g) and detector (dsd-dso=%g) must lie outside "
+                "the volume's circumscribed cylinder (radius %g)", geom->dso, geom->dsd - geom->dso, R);
+    const double vmax = 0.5 * (geom->nv - 1) * geom->dv;
+    MSF_REQUIRE(vmax < geom->dsd / sqrt(2.0),
+                "msf_projector_create: cone too wide (z-major rays are not modelled)");
+    MSF_REQUIRE((size_t)vol->nt * vol->nx * vol->ny * vol->nz < (size_t)1 << 40,
+                "msf_projector_create: volume too large");
+    MSF_TRY(check_device());
+
+    msf_projector* p = new msf_projector();
+    p->geom = *geom;
+    p->vol = *vol;
+    const int G = vol->nt * geom->views;
+    p->angles.assign(geom->angles, geom->angles + G);
+    p->geom.angles = p->angles.data();
+    ProjDims& d = p->dims;
+    d.nx = vol->nx; d.ny = vol->ny; d.nz = vol->nz; d.nt = vol->nt;
+    d.nu = geom->nu; d.nv = geom->nv; d.views = geom->views;
+    d.cx = 0.5f * (vol->nx - 1); d.cy = 0.5f * (vol->ny - 1); d.cz = 0.5f * (vol->nz - 1);
+    d.cu = 0.5f * (geom->nu - 1); d.cv = 0.5f * (geom->nv - 1);
+    d.vox = (float)vol->voxel; d.du = (float)geom->du; d.dv = (float)geom->dv;
+    d.dso = (float)geom->dso; d.dsd = (float)geom->dsd;
+
+    auto cleanup = [&](msf_status st) { msf_projector_destroy(p); return st; };
+    const size_t col_bytes = (size_t)G * geom->nu * 2 * sizeof(float4);
+    const size_t vol_bytes = vol_size(*vol) * sizeof(float);
+    if (cudaMalloc(&p->d_angles, G * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&p->d_col, col_bytes) != cudaSuccess ||
+        cudaMalloc(&p->d_trig, G * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&p->d_xT, vol_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(MSF_ERR_NOMEM, "msf_projector_create: out of device memory"));
+    }
+    p->bytes = G * sizeof(double) + col_bytes + G * sizeof(float2) + vol_bytes;
+    std::vector<float2> trig(G);
+    for (int g = 0; g < G; ++g) trig[g] = make_float2((float)cos(p->angles[g]), (float)sin(p->angles[g]));
+    int* d_bad = nullptr;
+    int h_bad = 0;
+    cudaError_t e = cudaMemcpy(p->d_angles, p->angles.data(), G * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_trig, trig.data(), G * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        column_table_kernel<<<dim3((geom->nu + 127) / 128, G), 128>>>(p->d_angles, p->d_col, d_bad, d, vol->voxel,
+                                                                    geom->du, geom->dso, geom->dsd);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (d_bad) cudaFree(d_bad);
+    if (e != cudaSuccess) return cleanup(fail(MSF_ERR_CUDA, "msf_projector_create: %s", cudaGetErrorString(e)));
+    if (h_bad) return cleanup(fail(MSF_ERR_ARG, "msf_projector_create: a ray's voxel planes are not all "
+                                               "between its source and detector"));
+    *out = p;
+    return MSF_OK;
+}
+
+extern "C" void msf_projector_destroy(msf_projector* p) {
+    if (!p) return;
+    cudaFree(p->d_angles);
+    cudaFree(p->d_col);
+    cudaFree(p->d_trig);
+    cudaFree(p->d_xT);
+    delete p;
+}
+
+extern "C" size_t msf_projector_bytes(const msf_projector* p) { return p ? p->bytes : 0; }
+
+extern "C" msf_status msf_project(msf_projector* p, const float* d_x, float* d_y, void* stream) {
+    MSF_REQUIRE(p && d_x && d_y, "msf_project: NULL argument");
+    return launch_fwd(p, FWD_PLAIN, d_x, d_y, nullptr, nullptr, as_stream(stream));
+}
+
+extern "C" msf_status msf_backproject(msf_projector* p, const float* d_y, float* d_x, void* stream) {
+    MSF_REQUIRE(p && d_x && d_y, "msf_backproject: NULL argument");
+    return launch_adj(p, ADJ_PLAIN, d_y, d_x, nullptr, nullptr, nullptr, nullptr, 0.0f, as_stream(stream));
+}
+
+extern "C" msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out) {
+    MSF_REQUIRE(p && out, "msf_dataprox_create: NULL argument");
+    *out = nullptr;
+    msf_dataprox* d = new msf_dataprox();
+    d->p = p;
+    const size_t nv = vol_size(p->vol), ns = sino_size(p);
+    const dim3 ga = adj_grid(p->dims);
+    d->parts_adj = ga.x * ga.y * p->vol.nz;
+    d->parts_upd = 512;
+    d->parts_max = d->parts_adj > d->parts_upd ? d->parts_adj : d->parts_upd;
+    const int nt = p->vol.nt;
+    if (cudaMalloc(&d->d_r, nv * 4) != cudaSuccess || cudaMalloc(&d->d_p, nv * 4) != cudaSuccess ||
+        cudaMalloc(&d->d_q, nv * 4) != cudaSuccess || cudaMalloc(&d->d_s, ns * 4) != cudaSuccess ||
+        cudaMalloc(&d->d_partial, (size_t)nt * d->parts_max * 8) != cudaSuccess ||
+        cudaMalloc(&d->d_rr, nt * 8) != cudaSuccess || cudaMalloc(&d->d_alpha, nt * 8) != cudaSuccess ||
+        cudaMalloc(&d->d_beta, nt * 8) != cudaSuccess || cudaMalloc(&d->d_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        msf_dataprox_destroy(d);
+        return fail(MSF_ERR_NOMEM, "msf_dataprox_create: out of device memory");
+    }
+    if (cudaMemset(d->d_status, 0, sizeof(int)) != cudaSuccess) {
+        msf_dataprox_destroy(d);
+        return fail(MSF_ERR_CUDA, "msf_dataprox_create: memset failed");
+    }
+    *out = d;
+    return MSF_OK;
+}
+
+extern "C" void msf_dataprox_destroy(msf_dataprox* d) {
+    if (!d) return;
+    cudaFree(d->d_r); cudaFree(d->d_p); cudaFree(d->d_q); cudaFree(d->d_s);
+    cudaFree(d->d_partial); cudaFree(d->d_rr); cudaFree(d->d_alpha); cudaFree(d->d_beta);
+    cudaFree(d->d_status);
+    delete d;
+}
+
+extern "C" msf_status msf_prox_data(msf_dataprox* dp, const float* d_y, const float* d_lambda,
+                                    const float* d_v, float* d_x, double sigma, int n_cg, void* stream) {
+    MSF_REQUIRE(dp && d_y && d_lambda && d_v && d_x, "msf_prox_data: NULL argument");
+    MSF_REQUIRE(sigma > 0 && isfinite(sigma), "msf_prox_data: sigma must be positive");
+    MSF_REQUIRE(n_cg >= 0, "msf_prox_data: n_cg must be >= 0");
+    if (n_cg == 0) return MSF_OK;
+    msf_projector* p = dp->p;
+    cudaStream_t st = as_stream(stream);
+    const float inv_s2 = (float)(1.0 / (sigma * sigma));
+    const int nt = p->vol.nt;
+    const size_t fs = frame_size(p->vol);
+    // r = A^T Lambda (y - A z) + (v - z)/sigma^2 ; p = r ; rr = r.r
+    MSF_TRY(launch_fwd(p, FWD_RESIDUAL, d_x, dp->d_s, d_lambda, d_y, st));
+    MSF_TRY(launch_adj(p, ADJ_CG_INIT, dp->d_s, dp->d_r, d_v, d_x, dp->d_p, dp->d_partial, inv_s2, st));
+    {
+        MSF_PROF("cg_finalize", st);
+        cg_finalize_kernel<FIN_RR0><<<nt, 256, 0, st>>>(dp->d_partial, dp->parts_adj, dp->d_rr, nullptr, dp->d_status);
+        MSF_LAUNCH_CHECK();
+    }
+    const msf_vol& v = p->vol;
+    const dim3 tgrid((v.nx + 31) / 32, (v.ny + 31) / 32, v.nz * v.nt);
+    for (int it = 0; it < n_cg; ++it) {
+        // p^T for the forward pass (fused with p = r + beta p after the first pass)
+        if (it == 0) {
+            MSF_TRY(launch_transpose(p, dp->d_p, p->d_xT, st));
+        } else {
+            MSF_PROF("transpose_pupdate", st);
+            transpose_kernel<true><<<tgrid, dim3(32, 8), 0, st>>>(nullptr, p->d_xT, dp->d_r, dp->d_p, dp->d_beta, v.nx, v.ny, v.nz);
+            MSF_LAUNCH_CHECK();
+        }
+        {   // s = Lambda A p  (transpose already in p->d_xT)
+            const ProjDims& d = p->dims;
+            dim3 grid((d.nu + 31) / 32, (d.nv + 3) / 4, d.nt * d.views);
+            MSF_PROF("joseph_fwd", st);
+            joseph_fwd_kernel<FWD_LAMBDA><<<grid, dim3(32, 4), 0, st>>>(dp->d_p, p->d_xT, p->d_col, dp->d_s, d_lambda, nullptr, d);
+            MSF_LAUNCH_CHECK();
+        }
+        // q = A^T s + p/sigma^2 ; alpha = rr / p.q
+        MSF_TRY(launch_adj(p, ADJ_CG_Q, dp->d_s, dp->d_q, dp->d_p, nullptr, nullptr, dp->d_partial, inv_s2, st));
+        {
+            MSF_PROF("cg_finalize", st);
+            cg_finalize_kernel<FIN_ALPHA><<<nt, 256, 0, st>>>(dp->d_partial, dp->parts_adj, dp->d_rr, dp->d_alpha, dp->d_status);
+            MSF_LAUNCH_CHECK();
+        }
+        {   // z += alpha p ; r -= alpha q ; beta = r.r / rr
+            MSF_PROF("cg_update", st);
+            cg_update_kernel<<<dim3(dp->parts_upd, nt), 256, 0, st>>>(d_x, dp->d_r, dp->d_p, dp->d_q, dp->d_alpha, dp->d_partial, fs);
+            MSF_LAUNCH_CHECK();
+        }
+        {
+            MSF_PROF("cg_finalize", st);
+            cg_finalize_kernel<FIN_BETA><<<nt, 256, 0, st>>>(dp->d_partial, dp->parts_upd, dp->d_rr, dp->d_beta, dp->d_status);
+            MSF_LAUNCH_CHECK();
+        }
+    }
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_phantom_voxelize(const msf_vol* vol, const double* h_ell, int n_ell, int ss,
+                                           float* d_x, void* stream) {
+    MSF_REQUIRE(vol && h_ell && d_x, "msf_phantom_voxelize: NULL argument");
+    MSF_REQUIRE(n_ell > 0 && ss > 0 && (size_t)n_ell * vol->nt <= MSF_MAX_ELL_RECORDS,
+                "msf_phantom_voxelize: need 0 < n_ell*nt <= %d and ss > 0", MSF_MAX_ELL_RECORDS);
+    cudaStream_t st = as_stream(stream);
+    MSF_TRY_CUDA(cudaMemcpyToSymbolAsync(c_ell, h_ell, (size_t)n_ell * vol->nt * 16 * sizeof(double), 0,
+                                         cudaMemcpyHostToDevice, st));
+    phantom_voxelize_kernel<<<152 * 8, 256, 0, st>>>(d_x, vol->nx, vol->ny, vol->nz, vol->nt, vol->voxel, n_ell, ss);
+    MSF_LAUNCH_CHECK();
+    MSF_TRY_CUDA(cudaStreamSynchronize(st));   // c_ell is reused by the next call
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_phantom_project(msf_projector* p, const double* h_ell, int n_ell, float* d_y,
+                                          void* stream) {
+    MSF_REQUIRE(p && h_ell && d_y, "msf_phantom_project: NULL argument");
+    MSF_REQUIRE(n_ell > 0 && (size_t)n_ell * p->vol.nt <= MSF_MAX_ELL_RECORDS,
+                "msf_phantom_project: need 0 < n_ell*nt <= %d", MSF_MAX_ELL_RECORDS);
+    cudaStream_t st = as_stream(stream);
+    MSF_TRY_CUDA(cudaMemcpyToSymbolAsync(c_ell, h_ell, (size_t)n_ell * p->vol.nt * 16 * sizeof(double), 0,
+                                         cudaMemcpyHostToDevice, st));
+    phantom_project_kernel<<<152 * 8, 256, 0, st>>>(p->d_angles, d_y, p->dims, p->geom.du, p->geom.dv,
+                                                    p->geom.dso, p->geom.dsd, n_ell);
+    MSF_LAUNCH_CHECK();
+    MSF_TRY_CUDA(cudaStreamSynchronize(st));
+    return MSF_OK;
+}
