@@ -25,8 +25,10 @@ struct MrfDims {
 
 // Surrogate coefficient a(D) = rho'(D)/(2D) of the q-GGMRF potential with p = 2:
 //   a(D) = 1/(2 sx^2) * (1 + (q/p) r)/(1 + r)^2,   r = |D/(T sx)|^(p-q).
+// r is formed as exp2((p-q) log2 |D/(T sx)|) with the hardware approximations
+// (about 2^-21 relative), far inside the FP32 tolerance of the agent.
 __device__ __forceinline__ float qggmrf_coef(float D, const MrfDims& m) {
-    const float r = powf(fabsf(D) * m.inv_tsx, m.pq);
+    const float r = m.pq == 0.0f ? 1.0f : exp2f(m.pq * __log2f(fabsf(D) * m.inv_tsx));
     const float op = 1.0f + r;
     return m.inv_2sx2 * (1.0f + m.q_over_p * r) / (op * op);
 }

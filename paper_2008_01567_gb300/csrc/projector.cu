@@ -69,8 +69,8 @@ __device__ __forceinline__ ColParams load_col(const float4* __restrict__ col, si
 // flags geometry the model does not cover: a plane crossing outside the
 // source-detector segment (0 < lambda < 1) on the first or last plane.
 __global__ void column_table_kernel(const double* __restrict__ angles, float4* __restrict__ col,
-                                    int* __restrict__ bad, ProjDims d, double vox, double du,
-                                    double dso, double dsd) {
+                                    int* __restrict__ vflag, int* __restrict__ bad, ProjDims d,
+                                    double vox, double du, double dso, double dsd) {
     const int iu = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = blockIdx.y;
     if (iu >= d.nu) return;
@@ -98,6 +98,7 @@ __global__ void column_table_kernel(const double* __restrict__ angles, float4* _
     const size_t idx = (size_t)g * d.nu + iu;
     col[2 * idx] = a;
     col[2 * idx + 1] = b;
+    atomicOr(vflag + g, xmaj ? 1 : 2);   // which major axes occur in this view
     const double lfirst = lam0 + (0 - 0.5 * (nmaj - 1)) * vox / dmaj;
     const double llast = lam0 + (nmaj - 1 - 0.5 * (nmaj - 1)) * vox / dmaj;
     if (!(fmin(lfirst, llast) > 0.0 && fmax(lfirst, llast) < 1.0)) atomicExch(bad, 1);
@@ -149,8 +150,10 @@ enum FwdMode { FWD_PLAIN = 0, FWD_LAMBDA = 1, FWD_RESIDUAL = 2 };
 // read the transposed frame [nz][nx][ny], y-major rays the natural frame
 // [nz][ny][nx], so in both cases the minor in-plane axis is contiguous.
 //   FWD_PLAIN:    out = A x
-//   FWD_LAMBDA:   out = Lambda * (A x)
-//   FWD_RESIDUAL: out = Lambda * (meas - A x)
+//   FWD_LAMBDA:   out = step * Lambda * (A x)
+//   FWD_RESIDUAL: out = step * Lambda * (meas - A x)
+// (the CG modes write the step-weighted sinogram e' = step * e that the gather
+// adjoint consumes)
 template <int MODE>
 __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     const float* __restrict__ x, const float* __restrict__ xT, const float4* __restrict__ col,
@@ -208,31 +211,42 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     const float val = acc * rz.step;
     const size_t ray = ((size_t)g * d.nv + iv) * d.nu + iu;
     if (MODE == FWD_PLAIN) out[ray] = val;
-    else if (MODE == FWD_LAMBDA) out[ray] = lam[ray] * val;
-    else out[ray] = lam[ray] * (meas[ray] - val);
+    else if (MODE == FWD_LAMBDA) out[ray] = rz.step * (lam[ray] * val);
+    else out[ray] = rz.step * (lam[ray] * (meas[ray] - val));
 }
 
 // ------------------------------------------------------------------ adjoint (gather)
 
 enum AdjMode { ADJ_PLAIN = 0, ADJ_CG_INIT = 1, ADJ_CG_Q = 2 };
 
-// Detector u coordinate (in pixels) of the point (x, y, .) for view (cs, sn).
+// Voxels of one z-run handled by one thread of the gather.
+constexpr int ADJ_ZB = 16;
+
+// Detector u coordinate (in pixels) of the point (x, y, .) for view (cs, sn);
+// only used to bound candidate columns, so a fast division is enough.
 __device__ __forceinline__ float u_pixel(float x, float y, float cs, float sn, const ProjDims& d) {
     const float lat = -x * sn + y * cs;
     const float depth = d.dso - x * cs - y * sn;
-    return d.dsd * lat / depth / d.du + d.cu;
+    return __fdividef(d.dsd * lat, depth) / d.du + d.cu;
 }
 
-// Sum over the rays of one view whose major axis is `XMAJ` of
-// w(ray, voxel) * e(ray).  For x-major rays the voxel is touched on plane
-// k = ix when floor(f_y) is iy-1 or iy; candidates are the detector columns
-// whose ray crosses that plane within one voxel of the centre in y (from the
-// exact projection of that segment, plus one column of margin), and on each
-// such column the rows whose f_z lies within one voxel of iz.
+// Adds, for the rays of one view whose major axis is XMAJ, w(ray, voxel) *
+// e'(ray) to the ADJ_ZB accumulators of the voxel run (ix, iy, iz_lo ..
+// iz_lo+ADJ_ZB-1), where e' = step * e is the step-weighted sinogram.
+//
+// An x-major ray touches column (ix, iy) on plane k = ix when floor(f_y) is
+// iy-1 or iy.  Candidate detector columns come from the exact projection of
+// the segment {x = x_ix, |y - y_iy| <= voxel} (plus one column of margin); on
+// a column that qualifies, the rows whose f_z(k) can fall within one voxel of
+// the run follow from f_z(v) = c_z + v (c1 + tk inv_dmaj).  Each ray's f_a and
+// f_z are then recomputed with the forward's own operations (ray_z, fmaf), so
+// its two z taps and its weights are those of the forward, bit for bit.
+// Every ray-plane crossing of the forward is visited by the two runs that hold
+// its a-taps, so the work tracks the forward's.
 template <bool XMAJ>
-__device__ __forceinline__ float gather_view(const float4* __restrict__ col,
-                                             const float* __restrict__ e, int g, int ix, int iy,
-                                             int iz, float cs, float sn, const ProjDims& d) {
+__device__ __forceinline__ void gather_runs(const float4* __restrict__ col, const float* __restrict__ e,
+                                            int g, int ix, int iy, int iz_lo, float cs, float sn,
+                                            const ProjDims& d, float (*acc)[128], int tid) {
     const int kpl = XMAJ ? ix : iy;             // plane index along the major axis
     const int ia = XMAJ ? iy : ix;              // voxel index on the minor axis
     const float cmaj = XMAJ ? d.cx : d.cy;
@@ -248,7 +262,7 @@ __device__ __forceinline__ float gather_view(const float4* __restrict__ col,
     const int iu_lo = max(0, (int)floorf(fminf(u1, u2)) - 1);
     const int iu_hi = min(d.nu - 1, (int)ceilf(fmaxf(u1, u2)) + 1);
     const float tk = __fsub_rn((float)kpl, cmaj);
-    float acc = 0.0f;
+    const float inv_dv = 1.0f / d.dv;
     for (int iu = iu_lo; iu <= iu_hi; ++iu) {
         const ColParams c = load_col(col, (size_t)g * d.nu + iu);
         if ((c.xmajor != 0.0f) != XMAJ) continue;
@@ -258,79 +272,100 @@ __device__ __forceinline__ float gather_view(const float4* __restrict__ col,
         if (ia != a0 && ia != a0 + 1) continue;
         const float wa1 = __fsub_rn(fa, a0f);
         const float wa = (ia == a0) ? __fsub_rn(1.0f, wa1) : wa1;
-        // f_z(v) = c_z + v (c1 + tk inv_dmaj): rows with f_z in (iz-1, iz+1)
-        const float gz = c.c1 + tk * c.inv_dmaj;
-        const float va = (iz - 1 - d.cz) / gz / d.dv + d.cv;
-        const float vb = (iz + 1 - d.cz) / gz / d.dv + d.cv;
-        const int iv_lo = max(0, (int)floorf(fminf(va, vb)) - 1);
-        const int iv_hi = min(d.nv - 1, (int)ceilf(fmaxf(va, vb)) + 1);
+        // rows with f_z in (iz_lo - 1, iz_lo + ADJ_ZB); gz > 0 (planes lie
+        // between source and detector)
+        const float rgz = __fdividef(1.0f, c.c1 + tk * c.inv_dmaj);
+        const float va = (iz_lo - 1 - d.cz) * rgz * inv_dv + d.cv;
+        const float vb = (iz_lo + ADJ_ZB - d.cz) * rgz * inv_dv + d.cv;
+        const int iv_lo = max(0, (int)floorf(va) - 1);
+        const int iv_hi = min(d.nv - 1, (int)ceilf(vb) + 1);
         const float* erow = e + ((size_t)g * d.nv) * d.nu + iu;
         for (int iv = iv_lo; iv <= iv_hi; ++iv) {
             const RayZ rz = ray_z(c, det_v(iv, d), d.cz);
             const float fz = __fmaf_rn(tk, rz.bz, rz.fz_mid);
             const float z0f = floorf(fz);
-            const int z0 = (int)z0f;
-            if (iz != z0 && iz != z0 + 1) continue;
+            const int k0 = (int)z0f - iz_lo;
+            if (k0 < -1 || k0 >= ADJ_ZB) continue;
             const float wz1 = __fsub_rn(fz, z0f);
-            const float wz = (iz == z0) ? __fsub_rn(1.0f, wz1) : wz1;
-            acc += rz.step * (wa * wz) * __ldg(erow + (size_t)iv * d.nu);
+            const float ev = wa * __ldg(erow + (size_t)iv * d.nu);
+            if (k0 >= 0) acc[k0][tid] += __fsub_rn(1.0f, wz1) * ev;
+            if (k0 + 1 < ADJ_ZB) acc[k0 + 1][tid] += wz1 * ev;
         }
     }
-    return acc;
 }
 
-// One thread per voxel; block 32 (x) x 4 (y) of one z-row pair.
+// One thread per run of ADJ_ZB voxels along z; block 32 (x) x 4 (y).
+// e is the step-weighted sinogram e' = step * e.
 //   ADJ_PLAIN:   out = A^T e
 //   ADJ_CG_INIT: r = A^T e + (v - z)/sigma^2, p = r, partial sum r.r
 //   ADJ_CG_Q:    q = A^T e + p/sigma^2, partial sum p.q
 template <int MODE>
 __global__ void __launch_bounds__(128) joseph_adj_kernel(
-    const float4* __restrict__ col, const float2* __restrict__ trig, const float* __restrict__ e,
-    float* __restrict__ out, const float* __restrict__ a1, const float* __restrict__ a2,
-    float* __restrict__ out2, double* __restrict__ partial, float inv_s2, ProjDims d) {
+    const float4* __restrict__ col, const float2* __restrict__ trig, const int* __restrict__ vflag,
+    const float* __restrict__ e, float* __restrict__ out, const float* __restrict__ a1,
+    const float* __restrict__ a2, float* __restrict__ out2, double* __restrict__ partial,
+    float inv_s2, ProjDims d) {
+    __shared__ float acc[ADJ_ZB][128];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     const int ix = blockIdx.x * 32 + threadIdx.x;
     const int iy = blockIdx.y * 4 + threadIdx.y;
-    const int iz = blockIdx.z % d.nz;
-    const int t = blockIdx.z / d.nz;
+    const int nzb = (d.nz + ADJ_ZB - 1) / ADJ_ZB;
+    const int zb = blockIdx.z % nzb;
+    const int t = blockIdx.z / nzb;
+    const int iz_lo = zb * ADJ_ZB;
     const bool inside = ix < d.nx && iy < d.ny;
-    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < ADJ_ZB; ++k) acc[k][tid] = 0.0f;
     if (inside) {
         for (int j = 0; j < d.views; ++j) {
             const int g = t * d.views + j;
             const float2 cs = __ldg(trig + g);
-            acc += gather_view<true>(col, e, g, ix, iy, iz, cs.x, cs.y, d);
-            acc += gather_view<false>(col, e, g, ix, iy, iz, cs.x, cs.y, d);
+            const int fl = __ldg(vflag + g);
+            if (fl & 1) gather_runs<true>(col, e, g, ix, iy, iz_lo, cs.x, cs.y, d, acc, tid);
+            if (fl & 2) gather_runs<false>(col, e, g, ix, iy, iz_lo, cs.x, cs.y, d, acc, tid);
         }
     }
-    const size_t i = (((size_t)t * d.nz + iz) * d.ny + iy) * d.nx + ix;
     double dot = 0.0;
-    if (MODE == ADJ_PLAIN) {
-        if (inside) out[i] = acc;
-    } else if (MODE == ADJ_CG_INIT) {
-        // a1 = v, a2 = z
-        if (inside) {
-            const float r = acc + (a1[i] - a2[i]) * inv_s2;
+    for (int k = 0; k < ADJ_ZB; ++k) {
+        const int iz = iz_lo + k;
+        if (!inside || iz >= d.nz) break;
+        const size_t i = (((size_t)t * d.nz + iz) * d.ny + iy) * d.nx + ix;
+        const float s = acc[k][tid];
+        if (MODE == ADJ_PLAIN) {
+            out[i] = s;
+        } else if (MODE == ADJ_CG_INIT) {   // a1 = v, a2 = z
+            const float r = s + (a1[i] - a2[i]) * inv_s2;
             out[i] = r;
             out2[i] = r;
-            dot = (double)r * (double)r;
-        }
-    } else {
-        // a1 = p
-        if (inside) {
+            dot += (double)r * (double)r;
+        } else {                            // a1 = p
             const float p = a1[i];
-            const float q = acc + p * inv_s2;
+            const float q = s + p * inv_s2;
             out[i] = q;
-            dot = (double)p * (double)q;
+            dot += (double)p * (double)q;
         }
     }
     if (MODE != ADJ_PLAIN) {
-        const double s = block_sum_f64(dot);
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const int bpf = gridDim.x * gridDim.y * d.nz;   // blocks per frame
-            const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * iz);
-            partial[(size_t)t * bpf + b] = s;
+        const double sum = block_sum_f64(dot);
+        if (tid == 0) {
+            const int bpf = gridDim.x * gridDim.y * nzb;   // blocks per frame
+            const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zb);
+            partial[(size_t)t * bpf + b] = sum;
         }
     }
+}
+
+// e' = step * e for every ray (input of the gather for a plain A^T).
+__global__ void step_weight_kernel(const float4* __restrict__ col, const float* __restrict__ e,
+                                   float* __restrict__ out, ProjDims d) {
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * 4 + threadIdx.y;
+    const int g = blockIdx.z;
+    if (iu >= d.nu || iv >= d.nv) return;
+    const ColParams c = load_col(col, (size_t)g * d.nu + iu);
+    const RayZ rz = ray_z(c, det_v(iv, d), d.cz);
+    const size_t ray = ((size_t)g * d.nv + iv) * d.nu + iu;
+    out[ray] = rz.step * e[ray];
 }
 
 // ------------------------------------------------------------------ CG scalars
@@ -470,7 +505,9 @@ struct msf_projector {
     double* d_angles = nullptr;
     float4* d_col = nullptr;
     float2* d_trig = nullptr;
+    int* d_vflag = nullptr;
     float* d_xT = nullptr;
+    float* d_sw = nullptr;     // step-weighted sinogram for msf_backproject
     size_t bytes = 0;
 };
 
@@ -517,7 +554,8 @@ static msf_status launch_fwd(msf_projector* p, int mode, const float* x, float* 
     return MSF_OK;
 }
 
-static dim3 adj_grid(const ProjDims& d) { return dim3((d.nx + 31) / 32, (d.ny + 3) / 4, d.nz * d.nt); }
+static int adj_nzb(const ProjDims& d) { return (d.nz + ADJ_ZB - 1) / ADJ_ZB; }
+static dim3 adj_grid(const ProjDims& d) { return dim3((d.nx + 31) / 32, (d.ny + 3) / 4, adj_nzb(d) * d.nt); }
 
 static msf_status launch_adj(msf_projector* p, int mode, const float* e, float* out,
                              const float* a1, const float* a2, float* out2, double* partial,
@@ -526,11 +564,11 @@ static msf_status launch_adj(msf_projector* p, int mode, const float* e, float* 
     dim3 grid = adj_grid(d), block(32, 4);
     MSF_PROF("joseph_adj", st);
     if (mode == ADJ_PLAIN)
-        joseph_adj_kernel<ADJ_PLAIN><<<grid, block, 0, st>>>(p->d_col, p->d_trig, e, out, a1, a2, out2, partial, inv_s2, d);
+        joseph_adj_kernel<ADJ_PLAIN><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
     else if (mode == ADJ_CG_INIT)
-        joseph_adj_kernel<ADJ_CG_INIT><<<grid, block, 0, st>>>(p->d_col, p->d_trig, e, out, a1, a2, out2, partial, inv_s2, d);
+        joseph_adj_kernel<ADJ_CG_INIT><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
     else
-        joseph_adj_kernel<ADJ_CG_Q><<<grid, block, 0, st>>>(p->d_col, p->d_trig, e, out, a1, a2, out2, partial, inv_s2, d);
+        joseph_adj_kernel<ADJ_CG_Q><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
 }
@@ -581,21 +619,25 @@ extern "C" msf_status msf_projector_create(const msf_geom* geom, const msf_vol* 
     if (cudaMalloc(&p->d_angles, G * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&p->d_col, col_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_trig, G * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&p->d_xT, vol_bytes) != cudaSuccess) {
+        cudaMalloc(&p->d_vflag, G * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->d_xT, vol_bytes) != cudaSuccess ||
+        cudaMalloc(&p->d_sw, sino_size(p) * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(MSF_ERR_NOMEM, "msf_projector_create: out of device memory"));
     }
-    p->bytes = G * sizeof(double) + col_bytes + G * sizeof(float2) + vol_bytes;
+    p->bytes = G * sizeof(double) + col_bytes + G * (sizeof(float2) + sizeof(int)) + vol_bytes +
+               sino_size(p) * sizeof(float);
     std::vector<float2> trig(G);
     for (int g = 0; g < G; ++g) trig[g] = make_float2((float)cos(p->angles[g]), (float)sin(p->angles[g]));
     int* d_bad = nullptr;
     int h_bad = 0;
     cudaError_t e = cudaMemcpy(p->d_angles, p->angles.data(), G * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_trig, trig.data(), G * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->d_vflag, 0, G * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
     if (e == cudaSuccess) {
-        column_table_kernel<<<dim3((geom->nu + 127) / 128, G), 128>>>(p->d_angles, p->d_col, d_bad, d, vol->voxel,
+        column_table_kernel<<<dim3((geom->nu + 127) / 128, G), 128>>>(p->d_angles, p->d_col, p->d_vflag, d_bad, d, vol->voxel,
                                                                     geom->du, geom->dso, geom->dsd);
         e = cudaGetLastError();
     }
@@ -613,7 +655,9 @@ extern "C" void msf_projector_destroy(msf_projector* p) {
     cudaFree(p->d_angles);
     cudaFree(p->d_col);
     cudaFree(p->d_trig);
+    cudaFree(p->d_vflag);
     cudaFree(p->d_xT);
+    cudaFree(p->d_sw);
     delete p;
 }
 
@@ -626,7 +670,15 @@ extern "C" msf_status msf_project(msf_projector* p, const float* d_x, float* d_y
 
 extern "C" msf_status msf_backproject(msf_projector* p, const float* d_y, float* d_x, void* stream) {
     MSF_REQUIRE(p && d_x && d_y, "msf_backproject: NULL argument");
-    return launch_adj(p, ADJ_PLAIN, d_y, d_x, nullptr, nullptr, nullptr, nullptr, 0.0f, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    {
+        const ProjDims& d = p->dims;
+        MSF_PROF("step_weight", st);
+        step_weight_kernel<<<dim3((d.nu + 31) / 32, (d.nv + 3) / 4, d.nt * d.views), dim3(32, 4), 0, st>>>(
+            p->d_col, d_y, p->d_sw, d);
+        MSF_LAUNCH_CHECK();
+    }
+    return launch_adj(p, ADJ_PLAIN, p->d_sw, d_x, nullptr, nullptr, nullptr, nullptr, 0.0f, st);
 }
 
 extern "C" msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out) {
@@ -636,7 +688,7 @@ extern "C" msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out) 
     d->p = p;
     const size_t nv = vol_size(p->vol), ns = sino_size(p);
     const dim3 ga = adj_grid(p->dims);
-    d->parts_adj = ga.x * ga.y * p->vol.nz;
+    d->parts_adj = ga.x * ga.y * adj_nzb(p->dims);
     d->parts_upd = 512;
     d->parts_max = d->parts_adj > d->parts_upd ? d->parts_adj : d->parts_upd;
     const int nt = p->vol.nt;

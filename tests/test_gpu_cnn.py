@@ -1,0 +1,144 @@
+"""GPU parity of the 2.5D CNN agents H_xy,t, H_yz,t, H_zx,t (Sec. IV, Eq. (14))
+against the FP64 oracle in BF16-emulating mode, through the C ABI.
+
+Tolerance: both sides round the network input, the folded weights and every
+stored hidden activation to BF16; they differ only in FP32 vs FP64 accumulation,
+which occasionally moves a stored activation by one BF16 step (2^-8 relative).
+Such flips stay sparse and partly cancel; over 9 stored layers the network
+output R = centre - H(x) keeps a relative L2 error of a few 1e-3, so 1e-2 is
+the bound used (on R, not on H(x), whose centre term is exact on both sides)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_01567_gb300 import synth
+from tests._problems import f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+ORIENT = {"xy": 0, "yz": 1, "zx": 2}
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    from paper_2008_01567_gb300 import build, msf
+    build.build()
+    assert torch.cuda.is_available()
+    return msf
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _net(seed):
+    rng = np.random.default_rng(seed)
+    convs, bns = synth.cnn_weights(seed)
+    convs = [(w, rng.normal(0, 0.05, b.shape)) for w, b in convs]
+    bns = [(g * rng.uniform(0.7, 1.3, g.shape), rng.normal(0, 0.1, g.shape)) for g, _ in bns]
+    stats = [(rng.normal(0, 0.1, 64), rng.uniform(0.5, 2.0, 64)) for _ in bns]
+    return convs, bns, stats
+
+
+def _gpu_net(M, convs, bns, stats, max_pixels):
+    c = M.Cnn(max_pixels)
+    flat = M.pack_params(convs, bns, stats)
+    c.set_params(flat)
+    # the oracle sees exactly the FP32 parameters the GPU holds
+    cv, bv, sv = M.unpack_params(flat)
+    return c, oracle.fold_bn(cv, bv, sv)
+
+
+@pytest.mark.parametrize("orient", ["xy", "yz", "zx"])
+def test_denoise_matches_oracle(M, orient):
+    import torch
+    convs, bns, stats = _net(51)
+    shape = (6, 18, 24, 20)                      # nt, nz, ny, nx: ragged against 16 x 8 tiles
+    v = f32(synth.uniform(52, shape, 0.0, 1.5))
+    c, layers = _gpu_net(M, convs, bns, stats, 2 * 24 * 20 * 18)
+    vol = M.msf_vol(shape[3], shape[2], shape[1], shape[0], 1.0)
+    out = torch.empty(shape, device="cuda")
+    M.msf_denoise(c, ORIENT[orient], vol, _t(v), out)
+    got_R = v - out.cpu().numpy()
+    ref_R = v - oracle.denoise(v, layers, orient, emulate_bf16=True)
+    assert rel_l2(got_R, ref_R) <= 1e-2
+    # and against the exact FP64 network: the BF16 pipeline stays close
+    ref64 = v - oracle.denoise(v, layers, orient, emulate_bf16=False)
+    assert rel_l2(got_R, ref64) <= 5e-2
+
+
+def test_zero_last_layer_returns_centre(M):
+    # A network whose last layer is zero returns the centre frame bit for bit.
+    import torch
+    convs, bns, stats = _net(53)
+    convs[-1] = (np.zeros_like(convs[-1][0]), np.zeros(1))
+    shape = (3, 9, 11, 13)
+    v = synth.uniform(54, shape)
+    c, _ = _gpu_net(M, convs, bns, stats, 4096)
+    vol = M.msf_vol(shape[3], shape[2], shape[1], shape[0], 1.0)
+    for o in range(3):
+        out = torch.full(shape, -7.0, device="cuda")
+        M.msf_denoise(c, o, vol, _t(v), out)
+        np.testing.assert_array_equal(out.cpu().numpy(), v.astype(np.float32))
+
+
+def test_single_frame_and_small_images(M):
+    # nt = 1: all five channels are the same frame; images smaller than a tile
+    import torch
+    convs, bns, stats = _net(55)
+    shape = (1, 5, 6, 7)
+    v = f32(synth.uniform(56, shape))
+    c, layers = _gpu_net(M, convs, bns, stats, 1024)
+    vol = M.msf_vol(shape[3], shape[2], shape[1], shape[0], 1.0)
+    for o in ("xy", "yz", "zx"):
+        out = torch.empty(shape, device="cuda")
+        M.msf_denoise(c, ORIENT[o], vol, _t(v), out)
+        assert rel_l2(v - out.cpu().numpy(), v - oracle.denoise(v, layers, o, emulate_bf16=True)) <= 1e-2
+
+
+def test_full_size_sampled_slices(M):
+    # the 384^3 x 16 workload in the benchmark's chunking (one time-point per
+    # chunk): sampled slices of every orientation against the oracle
+    import torch
+    scan = synth.FULL
+    convs, bns, stats = _net(57)
+    n, nt = scan.n, scan.nt
+    c, layers = _gpu_net(M, convs, bns, stats, n ** 3)
+    P = M.Projector(scan)
+    x = torch.empty((nt, n, n, n), device="cuda")
+    M.msf_phantom_voxelize(P.vol, synth.ellipsoids(58, 6, scan), x, ss=1)
+    x += 0.05 * torch.randn(x.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    out = torch.empty_like(x)
+    for o, (t, s) in (("xy", (0, 190)), ("yz", (15, 7)), ("zx", (8, 301))):
+        M.msf_denoise(c, ORIENT[o], P.vol, x, out)
+        torch.cuda.synchronize()
+        # oracle on the 5-frame window of one slice
+        tw = np.clip(np.arange(t - 2, t + 3), 0, nt - 1)
+        if o == "xy":
+            img = x[tw, s].cpu().numpy()                       # [5, y, x]
+            got = out[t, s].cpu().numpy()
+            cen = x[t, s].cpu().numpy()
+        elif o == "yz":
+            img = x[tw, :, :, s].cpu().numpy()                 # [5, z, y]
+            got = out[t, :, :, s].cpu().numpy()
+            cen = x[t, :, :, s].cpu().numpy()
+        else:
+            img = x[tw, :, s, :].cpu().numpy().transpose(0, 2, 1)   # [5, x, z]
+            got = out[t, :, s, :].cpu().numpy().T
+            cen = x[t, :, s, :].cpu().numpy().T
+        ref = oracle.cnn_forward(img[None].astype(np.float64), layers, emulate_bf16=True)[0]
+        assert rel_l2(cen - got, cen - ref) <= 1e-2, o
+
+
+def test_denoise_argument_errors(M):
+    c = M.Cnn(1000)
+    vol = M.msf_vol(16, 16, 16, 2, 1.0)
+    import torch
+    x = torch.zeros((2, 16, 16, 16), device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(M.MsfError) as e:
+        M.msf_denoise(c, 0, vol, x, y)      # one frame (4096 px) exceeds max_pixels
+    assert e.value.status == 1
+    with pytest.raises(M.MsfError):
+        M.msf_denoise(c, 5, vol, x, y)
