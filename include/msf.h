@@ -115,6 +115,27 @@ msf_status msf_project(msf_projector* p, const float* d_x, float* d_y, void* str
  * d_y: sinogram; d_x: 4D volume (overwritten). */
 msf_status msf_backproject(msf_projector* p, const float* d_y, float* d_x, void* stream);
 
+/* The forward projection of msf_project for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this entry exists for host
+ * applications that own the GPU's memory budget (their own pool or allocator,
+ * or a fixed footprint decided before work starts) and so cannot let a library
+ * call cudaMalloc, and for callers that must avoid cudaMalloc's implicit
+ * device-wide synchronisation.  It needs no projector plan: the per-column ray
+ * table is rebuilt on every call inside a fixed 8 MiB device array that the
+ * library defines statically, which every GPU that loads the library holds
+ * until the process exits.  The frame is read in its natural layout, so only
+ * the caller's d_x and d_y are touched besides that array.
+ * Limits: nt*views <= 8192 and nt*views*nu <= 250000; larger scans return
+ * MSF_ERR_ARG before any work is enqueued (use msf_projector_create +
+ * msf_project).  No cudaMalloc, cudaFree or other allocating call is made.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and each call overwrites it, so calls that may overlap
+ * on the GPU (different streams, different host threads) race and must be
+ * serialised by the caller.  Same layouts and result as msf_project. */
+msf_status msf_project_static(const msf_geom* geom, const msf_vol* vol, const float* d_x, float* d_y,
+                              void* stream);
+
 /* Measurement conditioning for M = nt*views*nv*nu rays:
  *   y = -ln(max(n,1)/I0)                (log-normalised counts)
  *   Lambda = c exp(-y)                   (Sec. II, the diagonal weight Lambda_n)

@@ -18,6 +18,7 @@
 //     step = sqrt(|d_xy|^2 + v^2) * voxel/|d_maj|.
 #include <math.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -801,5 +802,158 @@ extern "C" msf_status msf_phantom_project(msf_projector* p, const double* h_ell,
                                                     p->geom.dso, p->geom.dsd, n_ell);
     MSF_LAUNCH_CHECK();
     MSF_TRY_CUDA(cudaStreamSynchronize(st));
+    return MSF_OK;
+}
+
+// ====================================================================== no-allocation forward projection
+//
+// msf_project_static: the forward projection of msf_project for callers that
+// cannot allocate device memory.  The per-column ray table that a projector
+// plan would own lives instead in the file-scope device array below, of fixed
+// size, which every GPU that loads this library keeps until the process exits.
+// The frame is read in its natural layout for both ray families (no transposed
+// copy), so the caller's input and output are the only other memory touched.
+
+namespace msf {
+
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)8 << 20;   // 8 MiB
+constexpr int STATIC_MAX_VIEWS = 8192;                      // nt * views
+constexpr size_t STATIC_MAX_COLUMNS = 250000;               // nt * views * nu
+
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+// Layout inside the array: [angles: G doubles][column table: G*nu*32 B]
+// [view flags: G ints][geometry flag: 1 int].
+static_assert(STATIC_MAX_VIEWS * 8 + STATIC_MAX_COLUMNS * 32 + STATIC_MAX_VIEWS * 4 + 256 <= STATIC_SCRATCH_BYTES,
+              "static scratch too small for its stated limits");
+
+// Joseph forward projection reading the frame [nz][ny][nx] for both ray
+// families (same interpolation arithmetic as joseph_fwd_kernel; only the
+// addressing of x-major rays differs).
+__global__ void __launch_bounds__(128) joseph_fwd_direct_kernel(const float* __restrict__ x,
+                                                                const float4* __restrict__ col,
+                                                                float* __restrict__ out, ProjDims d) {
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * 4 + threadIdx.y;
+    const int g = blockIdx.z;
+    if (iu >= d.nu || iv >= d.nv) return;
+    const int t = g / d.views;
+    const ColParams c = load_col(col, (size_t)g * d.nu + iu);
+    const bool xmaj = c.xmajor != 0.0f;
+    const int nmaj = xmaj ? d.nx : d.ny, na = xmaj ? d.ny : d.nx;
+    const float* __restrict__ vol = x + (size_t)t * d.nx * d.ny * d.nz;
+    // element (iz, plane k, minor ia): x-major -> x[iz][ia][k], y-major -> x[iz][k][ia]
+    const ptrdiff_t s_maj = xmaj ? 1 : d.nx, s_min = xmaj ? d.nx : 1;
+    const ptrdiff_t s_z = (ptrdiff_t)d.nx * d.ny;
+    const float cmaj = xmaj ? d.cx : d.cy;
+    const RayZ rz = ray_z(c, det_v(iv, d), d.cz);
+    float acc = 0.0f;
+    for (int k = 0; k < nmaj; ++k) {
+        const float tk = __fsub_rn((float)k, cmaj);
+        const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
+        const float fz = __fmaf_rn(tk, rz.bz, rz.fz_mid);
+        const float a0f = floorf(fa), z0f = floorf(fz);
+        if (a0f < -1.0f || a0f > (float)(na - 1) || z0f < -1.0f || z0f > (float)(d.nz - 1)) continue;
+        const float wa1 = __fsub_rn(fa, a0f), wz1 = __fsub_rn(fz, z0f);
+        const int ia = (int)a0f, iz = (int)z0f;
+        const bool a_in0 = ia >= 0, a_in1 = ia + 1 < na;
+        const bool z_in0 = iz >= 0, z_in1 = iz + 1 < d.nz;
+        const float* p00 = vol + iz * s_z + k * s_maj + ia * s_min;
+        const float v00 = (z_in0 && a_in0) ? __ldg(p00) : 0.0f;
+        const float v01 = (z_in0 && a_in1) ? __ldg(p00 + s_min) : 0.0f;
+        const float v10 = (z_in1 && a_in0) ? __ldg(p00 + s_z) : 0.0f;
+        const float v11 = (z_in1 && a_in1) ? __ldg(p00 + s_z + s_min) : 0.0f;
+        const float wa0 = __fsub_rn(1.0f, wa1), wz0 = __fsub_rn(1.0f, wz1);
+        acc += wz0 * (wa0 * v00 + wa1 * v01) + wz1 * (wa0 * v10 + wa1 * v11);
+    }
+    out[((size_t)g * d.nv + iv) * d.nu + iu] = acc * rz.step;
+}
+
+// Device address of g_static_scratch for each device, looked up once per
+// device (with that device current) on the first call made on it.
+static std::mutex g_static_mu;
+static void* g_static_ptr[128] = {nullptr};
+
+}  // namespace msf
+
+extern "C" msf_status msf_project_static(const msf_geom* geom, const msf_vol* vol, const float* d_x, float* d_y,
+                                         void* stream) {
+    MSF_REQUIRE(geom && vol && d_x && d_y && geom->angles, "msf_project_static: NULL argument");
+    MSF_REQUIRE(vol->nx > 0 && vol->ny > 0 && vol->nz > 0 && vol->nt > 0 && vol->voxel > 0,
+                "msf_project_static: volume sizes and voxel must be positive");
+    MSF_REQUIRE(geom->nu > 0 && geom->nv > 0 && geom->views > 0 && geom->du > 0 && geom->dv > 0,
+                "msf_project_static: detector sizes, pitch and views must be positive");
+    const long long G = (long long)vol->nt * geom->views;
+    MSF_REQUIRE(G <= STATIC_MAX_VIEWS && (size_t)G * geom->nu <= STATIC_MAX_COLUMNS,
+                "msf_project_static: nt*views = %lld and nt*views*nu = %lld exceed the static table "
+                "(at most %d views and %zu view-columns); use msf_projector_create + msf_project",
+                G, G * geom->nu, STATIC_MAX_VIEWS, STATIC_MAX_COLUMNS);
+    const double R = 0.5 * vol->voxel * sqrt((double)vol->nx * vol->nx + (double)vol->ny * vol->ny);
+    MSF_REQUIRE(geom->dso > R && geom->dsd - geom->dso > R,
+                "msf_project_static: source and detector must lie outside the volume's circumscribed cylinder");
+    MSF_REQUIRE(0.5 * (geom->nv - 1) * geom->dv < geom->dsd / sqrt(2.0),
+                "msf_project_static: cone too wide (z-major rays are not modelled)");
+    // the voxel planes of every ray must lie between its source and detector
+    // (checked here in FP64 on the host, so no device flag has to be read back)
+    for (long long g = 0; g < G; ++g) {
+        const double th = geom->angles[g], c = cos(th), s = sin(th);
+        for (int iu = 0; iu < geom->nu; iu += geom->nu > 1 ? geom->nu - 1 : 1) {
+            const double u = (iu - 0.5 * (geom->nu - 1)) * geom->du;
+            const double sx = geom->dso * c, sy = geom->dso * s;
+            const double dx = -(geom->dsd - geom->dso) * c - u * s - sx, dy = -(geom->dsd - geom->dso) * s + u * c - sy;
+            const bool xm = fabs(dx) >= fabs(dy);
+            const double dmaj = xm ? dx : dy, smaj = xm ? sx : sy;
+            const int nmaj = xm ? vol->nx : vol->ny;
+            const double l1 = (-0.5 * (nmaj - 1) * vol->voxel - smaj) / dmaj;
+            const double l2 = (0.5 * (nmaj - 1) * vol->voxel - smaj) / dmaj;
+            MSF_REQUIRE(fmin(l1, l2) > 0.0 && fmax(l1, l2) < 1.0,
+                        "msf_project_static: a ray's voxel planes are not all between its source and detector");
+        }
+    }
+    int dev = 0;
+    MSF_TRY_CUDA(cudaGetDevice(&dev));
+    MSF_REQUIRE(dev >= 0 && dev < 128, "msf_project_static: device index %d out of range", dev);
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            MSF_TRY(check_device());
+            cudaError_t e = cudaGetSymbolAddress(&g_static_ptr[dev], g_static_scratch);
+            if (e != cudaSuccess) {
+                g_static_ptr[dev] = nullptr;
+                return fail(MSF_ERR_CUDA, "msf_project_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            }
+        }
+        base = g_static_ptr[dev];
+    }
+    unsigned char* b = static_cast<unsigned char*>(base);
+    double* d_angles = reinterpret_cast<double*>(b);
+    float4* d_col = reinterpret_cast<float4*>(b + (size_t)STATIC_MAX_VIEWS * 8);
+    int* d_vflag = reinterpret_cast<int*>(b + (size_t)STATIC_MAX_VIEWS * 8 + STATIC_MAX_COLUMNS * 32);
+    int* d_bad = d_vflag + STATIC_MAX_VIEWS;
+    ProjDims d;
+    d.nx = vol->nx; d.ny = vol->ny; d.nz = vol->nz; d.nt = vol->nt;
+    d.nu = geom->nu; d.nv = geom->nv; d.views = geom->views;
+    d.cx = 0.5f * (vol->nx - 1); d.cy = 0.5f * (vol->ny - 1); d.cz = 0.5f * (vol->nz - 1);
+    d.cu = 0.5f * (geom->nu - 1); d.cv = 0.5f * (geom->nv - 1);
+    d.vox = (float)vol->voxel; d.du = (float)geom->du; d.dv = (float)geom->dv;
+    d.dso = (float)geom->dso; d.dsd = (float)geom->dsd;
+    cudaStream_t st = as_stream(stream);
+    // the array keeps the previous call's contents: the flags start at zero
+    MSF_TRY_CUDA(cudaMemcpyAsync(d_angles, geom->angles, G * sizeof(double), cudaMemcpyHostToDevice, st));
+    MSF_TRY_CUDA(cudaMemsetAsync(d_vflag, 0, G * sizeof(int), st));
+    MSF_TRY_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    {
+        MSF_PROF("column_table", st);
+        column_table_kernel<<<dim3((geom->nu + 127) / 128, (unsigned)G), 128, 0, st>>>(
+            d_angles, d_col, d_vflag, d_bad, d, vol->voxel, geom->du, geom->dso, geom->dsd);
+        MSF_LAUNCH_CHECK();
+    }
+    {
+        MSF_PROF("joseph_fwd_direct", st);
+        joseph_fwd_direct_kernel<<<dim3((d.nu + 31) / 32, (d.nv + 3) / 4, (unsigned)G), dim3(32, 4), 0, st>>>(
+            d_x, d_col, d_y, d);
+        MSF_LAUNCH_CHECK();
+    }
     return MSF_OK;
 }

@@ -69,6 +69,7 @@ _SIGS = {
     "msf_projector_bytes": (_Z, [_P]),
     "msf_project": (_I, [_P, _P, _P, _P]),
     "msf_backproject": (_I, [_P, _P, _P, _P]),
+    "msf_project_static": (_I, [ctypes.POINTER(msf_geom), ctypes.POINTER(msf_vol), _P, _P, _P]),
     "msf_weights": (_I, [_P, _P, _P, _Z, _D, _D, _P]),
     "msf_dataprox_create": (_I, [_P, ctypes.POINTER(_P)]),
     "msf_dataprox_destroy": (None, [_P]),
@@ -192,6 +193,16 @@ def msf_project(proj: Projector, x, y, stream=None):
 
 def msf_backproject(proj: Projector, y, x, stream=None):
     _check(lib().msf_backproject(proj.handle, _f32(y), _f32(x), _stream(stream)))
+
+
+def msf_project_static(scan, x, y, angles=None, stream=None):
+    """Forward projection without a plan and without any device allocation
+    (the ray table lives in the library's fixed static device array)."""
+    ang = np.ascontiguousarray(scan.angles() if angles is None else angles, dtype=np.float64).ravel()
+    geom = msf_geom(scan.nu, scan.nv, scan.views, scan.pitch, scan.pitch, scan.dso, scan.dsd,
+                    ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    vol = vol_of(scan)
+    _check(lib().msf_project_static(ctypes.byref(geom), ctypes.byref(vol), _f32(x), _f32(y), _stream(stream)))
 
 
 def msf_weights(counts, y, lam, I0: float, c: float, stream=None):
