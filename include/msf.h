@@ -222,6 +222,27 @@ msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* vol,
 msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const float* d_clean,
                           int B, int H, int W, float lr, float* h_loss, void* stream);
 
+/* Reserves the training workspace for batches of up to max_train_pixels =
+ * B*H*W pixels (about 3.7 KB per pixel: every layer's BF16 activations, FP32
+ * pre-BatchNorm outputs, gradients and reduction buffers).  Must precede
+ * msf_train_step; a larger reservation replaces a smaller one. */
+msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels);
+
+/* Copies the gradients of the last msf_train_step (flat layout of
+ * msf_cnn_get_params; the running-statistics entries are zero). */
+msf_status msf_cnn_get_grads(msf_cnn* c, float* h_grads, size_t n);
+
+/* Training pairs (Sec. V: clean patches plus additive white Gaussian noise):
+ * B patches of H x W with 5 channels cut from the clean volume stack d_vol
+ * (vol->nt volumes of nx*ny*nz).  Each patch takes a random volume, a random
+ * slicing axis whose 5 adjacent slices (clamped) stand in for the 5
+ * time-points, a random slice and position, a random flip/transpose, and
+ * noise sigma ~ U[sigma_lo, sigma_hi]; every channel gets independent
+ * N(0, sigma^2) noise from a counter-based hash of (seed, element).
+ * d_noisy: [B][5][H][W]; d_clean: [B][H][W] (the clean centre slice). */
+msf_status msf_training_batch(const float* d_vol, const msf_vol* vol, int B, int H, int W, double sigma_lo,
+                              double sigma_hi, uint64_t seed, float* d_noisy, float* d_clean, void* stream);
+
 /* ------------------------------------------------------------ MACE */
 
 typedef enum { MSF_PRIOR_QGGMRF = 0, MSF_PRIOR_CNN = 1 } msf_prior_kind;

@@ -394,18 +394,23 @@ def denoise(v4, layers, orient, emulate_bf16=False):
 # ---- training (Sec. V): MSE on (noisy, clean) pairs, BatchNorm in training mode, Adam.
 
 
-def train_forward(x, convs, bns):
+def train_forward(x, convs, bns, emulate_bf16=False):
     """Training forward; returns (out, cache).  Hidden layers: conv (+bias),
-    BatchNorm with batch statistics (biased variance), ReLU."""
-    cache = {"a": [x], "z": [], "xhat": [], "istd": [], "y": [], "stats": []}
-    a = x
+    BatchNorm with batch statistics (biased variance), ReLU.
+    With emulate_bf16, the points where a BF16 implementation stores values are
+    rounded to BF16: the network input, every conv weight, and every
+    activation after ReLU; pre-BatchNorm outputs and the last layer's output
+    stay unrounded (FP64 here)."""
+    r = bf16 if emulate_bf16 else (lambda t: t)
+    cache = {"a": [r(x)], "z": [], "xhat": [], "istd": [], "y": [], "stats": [], "emulate": emulate_bf16}
+    a = r(x)
     L = len(convs)
     for l in range(L):
         w, b = convs[l]
-        z = conv3x3(a, w, b)
+        z = conv3x3(a, r(w), b)
         cache["z"].append(z)
         if l == 0:
-            a = np.maximum(z, 0.0)
+            a = r(np.maximum(z, 0.0))
         elif l < L - 1:
             g, be = bns[l - 1]
             mean = z.mean(axis=(0, 2, 3))
@@ -417,7 +422,7 @@ def train_forward(x, convs, bns):
             cache["istd"].append(istd)
             cache["y"].append(yv)
             cache["stats"].append((mean, var))
-            a = np.maximum(yv, 0.0)
+            a = r(np.maximum(yv, 0.0))
         else:
             a = z
         if l < L - 1:
@@ -426,10 +431,16 @@ def train_forward(x, convs, bns):
     return out, cache
 
 
-def train_loss_grad(x, clean, convs, bns):
+def train_loss_grad(x, clean, convs, bns, emulate_bf16=False):
     """MSE loss mean((out - clean)^2) and its gradients w.r.t. every conv weight,
-    conv bias and BatchNorm gamma/beta.  Returns (loss, gconvs, gbns, stats)."""
-    out, c = train_forward(x, convs, bns)
+    conv bias and BatchNorm gamma/beta.  Returns (loss, gconvs, gbns, stats).
+    With emulate_bf16, besides the forward's rounding (train_forward), the
+    gradients that a BF16 implementation stores between layers are rounded:
+    the input gradient of every layer below the last, and the pre-activation
+    gradient dz of every layer below the last; the last layer's input
+    gradient is formed with FP32 weights, the others with the rounded ones."""
+    r = bf16 if emulate_bf16 else (lambda t: t)
+    out, c = train_forward(x, convs, bns, emulate_bf16)
     L = len(convs)
     npx = out.size
     loss = float(np.mean((out - clean) ** 2))
@@ -441,7 +452,7 @@ def train_loss_grad(x, clean, convs, bns):
         if l == L - 1:
             dz = da
         elif l == 0:
-            dz = da * (c["z"][0] > 0)
+            dz = r(da * (c["z"][0] > 0))
         else:
             dy = da * (c["y"][l - 1] > 0)
             xhat, istd = c["xhat"][l - 1], c["istd"][l - 1]
@@ -450,11 +461,12 @@ def train_loss_grad(x, clean, convs, bns):
             dxh = dy * g[None, :, None, None]
             m1 = dxh.mean(axis=(0, 2, 3))[None, :, None, None]
             m2 = (dxh * xhat).mean(axis=(0, 2, 3))[None, :, None, None]
-            dz = istd[None, :, None, None] * (dxh - m1 - xhat * m2)
+            dz = r(istd[None, :, None, None] * (dxh - m1 - xhat * m2))
         a_in = c["a"][l]
         gconvs[l] = (conv3x3_wgrad(dz, a_in), dz.sum(axis=(0, 2, 3)))
         if l > 0:
-            da = conv3x3_dgrad(dz, convs[l][0])
+            w = convs[l][0] if l == L - 1 else r(convs[l][0])
+            da = r(conv3x3_dgrad(dz, w))
     return loss, gconvs, gbns, c["stats"]
 
 

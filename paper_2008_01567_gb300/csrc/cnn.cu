@@ -44,7 +44,15 @@ constexpr int HALO_BYTES = (TILE_A + 2) * TILE_B * 128;   // 18432
 constexpr int TILE_BYTES = TILE_A * TILE_B * 128;         // 16384
 constexpr int TMEM_COLS = 128;
 
-enum Epi { EPI_RELU = 0, EPI_RESID = 1 };
+// EPI_RELU:  relu(acc + bias) -> BF16 activations (TMA store)
+// EPI_RAW:   acc + bias -> BF16 (TMA store): pre-BatchNorm outputs and input gradients
+// EPI_RESID: last layer, centre - (acc + bias) -> FP32 4D output volume
+// EPI_F32:   last layer, acc + bias -> FP32 [img][H][W] (training)
+// EPI_RAW32: acc + bias -> FP32 [img][H][W][64] (training: pre-BatchNorm outputs,
+//            kept in FP32 because normalising subtracts their batch mean)
+enum Epi { EPI_RELU = 0, EPI_RESID = 1, EPI_RAW = 2, EPI_F32 = 3, EPI_RAW32 = 4 };
+
+__host__ __device__ constexpr bool epi_stores_bf16(int e) { return e == EPI_RELU || e == EPI_RAW; }
 
 // Flat FP32 parameter layout (see msf.h): W_l, b_l for l = 0..9, then gamma,
 // beta, running mean, running var for the 8 BatchNorm layers.
@@ -202,7 +210,7 @@ template <int TAPS, int N, int NS, int EPI>
 struct ConvCfg {
     static constexpr int A_BYTES = TAPS == 9 ? 3 * HALO_BYTES : TILE_BYTES;
     static constexpr int W_BYTES = TAPS * N * 128;
-    static constexpr int O_BYTES = EPI == EPI_RELU ? 2 * TILE_BYTES : 0;
+    static constexpr int O_BYTES = epi_stores_bf16(EPI) ? 2 * TILE_BYTES : 0;
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM = 1024 + NS * A_BYTES + W_BYTES + O_BYTES + BAR_BYTES;
 };
@@ -344,12 +352,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             tc::mbar_arrive(&tempty[ab]);
             int img, a0, b0;
             decode_tile(tg, tile, img, a0, b0);
-            if (EPI == EPI_RELU) {
+            if (epi_stores_bf16(EPI)) {
                 uint32_t w[N / 2];
 #pragma unroll
                 for (int j = 0; j < N / 2; ++j) {
-                    const float lo = fmaxf(__uint_as_float(r[2 * j]) + __ldg(bias + 2 * j), 0.0f);
-                    const float hi = fmaxf(__uint_as_float(r[2 * j + 1]) + __ldg(bias + 2 * j + 1), 0.0f);
+                    float lo = __uint_as_float(r[2 * j]) + __ldg(bias + 2 * j);
+                    float hi = __uint_as_float(r[2 * j + 1]) + __ldg(bias + 2 * j + 1);
+                    if (EPI == EPI_RELU) {
+                        lo = fmaxf(lo, 0.0f);
+                        hi = fmaxf(hi, 0.0f);
+                    }
                     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
                     w[j] = *reinterpret_cast<uint32_t*>(&h);
                 }
@@ -370,17 +382,32 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                     if (a0 + q * (TILE_A / 4) < tg.H) tc::tma_store_4d(&map_out, stage, 0, b0, a0 + q * (TILE_A / 4), img);
                     tc::tma_store_commit();
                 }
+            } else if (EPI == EPI_RAW32) {
+                const int a = a0 + row / TILE_B, b = b0 + row % TILE_B;
+                if (a < tg.H && b < tg.W) {
+                    float4* dst = reinterpret_cast<float4*>(outv + (((size_t)img * tg.H + a) * tg.W + b) * N);
+#pragma unroll
+                    for (int j = 0; j < N / 4; ++j)
+                        dst[j] = make_float4(__uint_as_float(r[4 * j]) + __ldg(bias + 4 * j),
+                                             __uint_as_float(r[4 * j + 1]) + __ldg(bias + 4 * j + 1),
+                                             __uint_as_float(r[4 * j + 2]) + __ldg(bias + 4 * j + 2),
+                                             __uint_as_float(r[4 * j + 3]) + __ldg(bias + 4 * j + 3));
+                }
             } else {
                 const float R = __uint_as_float(r[0]) + __ldg(bias);
                 const int a = a0 + row / TILE_B, b = b0 + row % TILE_B;
                 if (a < tg.H && b < tg.W) {
-                    const int t = sg.t0 + img / sg.S, s = img % sg.S;
-                    const size_t idx = vol_index(sg, t, s, a, b);
-                    outv[idx] = centre[idx] - R;
+                    if (EPI == EPI_RESID) {
+                        const int t = sg.t0 + img / sg.S, s = img % sg.S;
+                        const size_t idx = vol_index(sg, t, s, a, b);
+                        outv[idx] = centre[idx] - R;
+                    } else {
+                        outv[((size_t)img * tg.H + a) * tg.W + b] = R;
+                    }
                 }
             }
         }
-        if (EPI == EPI_RELU && lane == 0) tc::tma_store_wait_all();
+        if (epi_stores_bf16(EPI) && lane == 0) tc::tma_store_wait_all();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -459,7 +486,10 @@ static msf_status launch_conv(const CUtensorMap& ma, const CUtensorMap& mw, cons
     }
     const int grid = tg.total < g_num_sms ? tg.total : g_num_sms;
     if (grid <= 0) return MSF_OK;
-    MSF_PROF(TAPS == 1 ? "conv1_tc" : (EPI == EPI_RESID ? "conv10_tc" : "conv3x3_tc"), st);
+    MSF_PROF(TAPS == 1 ? "conv1_tc"
+                       : (N == 16 ? "conv10_tc"
+                                  : (EPI == EPI_RAW ? "conv3x3_dgrad_tc" : (EPI == EPI_RAW32 ? "conv3x3_fp32_tc" : "conv3x3_tc"))),
+             st);
     kern<<<grid, THREADS, C::SMEM, st>>>(ma, mw, mo, bias, tg, sg, centre, outv, err);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
@@ -480,6 +510,7 @@ struct msf_cnn {
     float* d_grad = nullptr;
     float* d_m = nullptr;           // Adam moments
     float* d_v = nullptr;
+    uint8_t* d_frozen = nullptr;    // 1 for parameters Adam leaves alone (running statistics)
     __nv_bfloat16* d_wpack = nullptr;
     float* d_bias = nullptr;        // [10][64]
     size_t wpack_off[LAYERS];
@@ -487,7 +518,8 @@ struct msf_cnn {
     int* d_err = nullptr;
     bool folded = false;
     int64_t adam_t = 0;
-    // training workspace (allocated on first use by msf_train_step)
+    // training workspace (msf_cnn_train_reserve)
+    int64_t train_cap = 0;
     void* train_ws = nullptr;
     size_t train_ws_bytes = 0;
 };
@@ -536,7 +568,7 @@ extern "C" msf_status msf_cnn_create(int64_t max_pixels, msf_cnn** out) {
               cudaMalloc(&c->d_m, P * 4) == cudaSuccess && cudaMalloc(&c->d_v, P * 4) == cudaSuccess &&
               cudaMalloc(&c->d_wpack, wp * 2) == cudaSuccess && cudaMalloc(&c->d_bias, LAYERS * CH * 4) == cudaSuccess &&
               cudaMalloc(&c->d_act[0], act) == cudaSuccess && cudaMalloc(&c->d_act[1], act) == cudaSuccess &&
-              cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess;
+              cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess && cudaMalloc(&c->d_frozen, P) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         msf_cnn_destroy(c);
@@ -546,6 +578,13 @@ extern "C" msf_status msf_cnn_create(int64_t max_pixels, msf_cnn** out) {
     cudaMemset(c->d_m, 0, P * 4);
     cudaMemset(c->d_v, 0, P * 4);
     cudaMemset(c->d_err, 0, sizeof(int));
+    {
+        std::vector<uint8_t> frozen(P, 0);
+        for (int l = 1; l < LAYERS - 1; ++l)
+            for (int k = 0; k < CH; ++k) frozen[c->off.mean[l] + k] = frozen[c->off.var[l] + k] = 1;
+        cudaMemcpy(c->d_frozen, frozen.data(), P, cudaMemcpyHostToDevice);
+        cudaMemset(c->d_grad, 0, P * 4);
+    }
     *out = c;
     return MSF_OK;
 }
@@ -556,6 +595,7 @@ extern "C" void msf_cnn_destroy(msf_cnn* c) {
     cudaFree(c->d_wpack); cudaFree(c->d_bias);
     cudaFree(c->d_act[0]); cudaFree(c->d_act[1]);
     cudaFree(c->d_err);
+    cudaFree(c->d_frozen);
     cudaFree(c->train_ws);
     delete c;
 }
@@ -637,6 +677,747 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
     return MSF_OK;
 }
 
-extern "C" msf_status msf_train_step(msf_cnn*, const float*, const float*, int, int, int, float, float*, void*) {
-    return msf::fail(MSF_ERR_UNSUPPORTED, "msf_train_step: not built yet");
+// ====================================================================== training (Sec. V)
+//
+// One step on a batch of B noisy 5-frame patches [B][5][H][W] and clean centre
+// slices [B][H][W]: forward with BatchNorm batch statistics, loss
+// mean((centre - R - clean)^2), backward, Adam on the FP32 master parameters.
+// Activations and gradients between layers are BF16 [P][64] (P = B*H*W);
+// reductions (BatchNorm statistics, loss, weight gradients) are FP32/FP64.
+//   forward convs: tcgen05 (layer 1 on the packed 45-value neighbourhoods,
+//                  hidden layers with EPI_RAW, last layer with EPI_F32)
+//   input grads:   tcgen05 with the transposed, flipped kernels
+//                  W'[tap'][ci][co] = W[co][ci][2-ky][2-kx]
+//   weight grads:  FP32 SIMT reduction over pixels, split into chunks and
+//                  summed in a fixed order.
+
+namespace msf {
+namespace cnn {
+
+constexpr float BN_MOMENTUM = 0.1f;
+constexpr int WG_CHUNK = 4096;      // pixels per weight-gradient block
+
+// Workspace carved from one allocation.
+struct TrainWS {
+    __nv_bfloat16* act[LAYERS];     // act[0] packed input, act[l] output of layer l-1 (l = 1..9)
+    float* z[LAYERS];               // z[l], l = 1..8: pre-BatchNorm conv outputs (FP32)
+    __nv_bfloat16* g[2];            // gradient ping-pong
+    float* R;                       // last-layer output
+    float* dR;
+    double* part;                   // reduction partials
+    double* sums;                   // [8][4][64]: sum z, sum z^2, sum dy, sum dy*xhat
+    float* bnp;                     // [8][2][64]: mean, istd of the batch
+    float* wpart;                   // weight-gradient partials
+    __nv_bfloat16* wf;              // packed forward weights (no BatchNorm folding)
+    __nv_bfloat16* wb;              // packed input-gradient weights, layers 1..8
+    float* bf;                      // [10][64] forward biases
+    float* zeros;                   // [64]
+    double* loss;                   // [1]
+    int nchunks, nred;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t train_layout(int64_t P, TrainWS* w, uint8_t* base) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        uint8_t* p = base ? base + o : nullptr;
+        o += align256(bytes);
+        return p;
+    };
+    const size_t act = (size_t)P * CH * 2;
+    TrainWS t{};
+    for (int l = 0; l < LAYERS; ++l) t.act[l] = (__nv_bfloat16*)take(act);
+    for (int l = 1; l < LAYERS - 1; ++l) t.z[l] = (float*)take(act * 2);
+    t.g[0] = (__nv_bfloat16*)take(act);
+    t.g[1] = (__nv_bfloat16*)take(act);
+    t.R = (float*)take((size_t)P * 4);
+    t.dR = (float*)take((size_t)P * 4);
+    t.nchunks = (int)((P + WG_CHUNK - 1) / WG_CHUNK);
+    t.nred = 2 * 152;
+    t.part = (double*)take((size_t)t.nred * 2 * CH * 8);
+    t.sums = (double*)take((size_t)8 * 4 * CH * 8);
+    t.bnp = (float*)take((size_t)8 * 2 * CH * 4);
+    t.wpart = (float*)take((size_t)t.nchunks * 9 * CH * CH * 4);
+    size_t wp = 0;
+    for (int l = 0; l < LAYERS; ++l) wp += (size_t)taps_of(l) * rows_of(l) * KPACK;
+    t.wf = (__nv_bfloat16*)take(wp * 2);
+    t.wb = (__nv_bfloat16*)take((size_t)8 * 9 * CH * CH * 2);
+    t.bf = (float*)take(LAYERS * CH * 4);
+    t.zeros = (float*)take(CH * 4);
+    t.loss = (double*)take(8);
+    if (w) *w = t;
+    return o;
+}
+
+// [B][5][H][W] FP32 -> packed BF16 [B][H][W][64] (k = frame*9 + ky*3 + kx).
+__global__ void pack_batch_kernel(const float* __restrict__ x, uint4* __restrict__ out, int B, int H, int W) {
+    const size_t total = (size_t)B * H * W;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(p % W), a = (int)((p / W) % H), img = (int)(p / ((size_t)H * W));
+        float v[FRAMES * 9];
+#pragma unroll
+        for (int c = 0; c < FRAMES; ++c)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int aa = a + ky - 1, bb = b + kx - 1;
+                    v[c * 9 + ky * 3 + kx] = (aa >= 0 && aa < H && bb >= 0 && bb < W)
+                                                 ? x[(((size_t)img * FRAMES + c) * H + aa) * W + bb] : 0.0f;
+                }
+        uint32_t w[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(2 * i < 45 ? v[2 * i] : 0.0f, 2 * i + 1 < 45 ? v[2 * i + 1] : 0.0f);
+            w[i] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        uint4* dst = out + p * 8;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) dst[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+    }
+}
+
+// Input-gradient kernels of the hidden layers: W'[tap'][ci][co] = W[co][ci][2-ky][2-kx].
+__global__ void pack_dgrad_kernel(const float* __restrict__ params, __nv_bfloat16* __restrict__ wb, Offsets o) {
+    const int n = 8 * 9 * CH * CH;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int l = 1 + e / (9 * CH * CH);
+        const int r = e % (9 * CH * CH);
+        const int tap = r / (CH * CH), ci = (r / CH) % CH, co = r % CH;
+        const int ky = 2 - tap / 3, kx = 2 - tap % 3;
+        wb[e] = __float2bfloat16_rn(params[o.w[l] + ((size_t)co * CH + ci) * 9 + ky * 3 + kx]);
+    }
+}
+
+__device__ __forceinline__ void bf16x8_to_f32(uint4 u, float* f) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        f[2 * i] = __uint_as_float(w[i] << 16);
+        f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+}
+
+__device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        w[i] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+enum RedMode { RED_MOMENTS = 0, RED_BNBWD = 1, RED_SUM = 2 };
+
+// Per-channel sums over P pixels of [P][64] BF16 tensors; 256 threads = 8
+// lanes of 8 channels x 32 pixel rows.  Writes FP64 partials [block][2][64].
+//   RED_MOMENTS: sum z, sum z^2                     (z = t0, FP32)
+//   RED_BNBWD:   sum dy, sum dy*xhat with dy = g * [gamma xhat + beta > 0],
+//                xhat = (z - mean) istd               (g = t0 BF16, z = t1 FP32)
+//   RED_SUM:     sum t0                               (BF16)
+__device__ __forceinline__ void f32x8_load(const float* p, float* f) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restrict__ t0v, const float* __restrict__ t1,
+                                                             const float* __restrict__ bnp, const float* __restrict__ gamma,
+                                                             const float* __restrict__ beta, size_t P,
+                                                             double* __restrict__ part) {
+    __shared__ double sh[2][32][65];
+    const int lane8 = threadIdx.x & 7, row = threadIdx.x >> 3;
+    double s0[8], s1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s0[i] = s1[i] = 0.0;
+    float mean[8], istd[8], ga[8], be[8];
+    if (MODE == RED_BNBWD) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            mean[i] = bnp[lane8 * 8 + i];
+            istd[i] = bnp[CH + lane8 * 8 + i];
+            ga[i] = gamma[lane8 * 8 + i];
+            be[i] = beta[lane8 * 8 + i];
+        }
+    }
+    for (size_t p = blockIdx.x * (size_t)32 + row; p < P; p += (size_t)gridDim.x * 32) {
+        float a[8];
+        if (MODE == RED_MOMENTS) f32x8_load(static_cast<const float*>(t0v) + p * CH + lane8 * 8, a);
+        else bf16x8_to_f32(static_cast<const uint4*>(t0v)[p * 8 + lane8], a);
+        if (MODE == RED_MOMENTS) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { s0[i] += a[i]; s1[i] += (double)a[i] * a[i]; }
+        } else if (MODE == RED_SUM) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s0[i] += a[i];
+        } else {
+            float z[8];
+            f32x8_load(t1 + p * CH + lane8 * 8, z);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float xh = (z[i] - mean[i]) * istd[i];
+                const float dy = (ga[i] * xh + be[i] > 0.0f) ? a[i] : 0.0f;
+                s0[i] += dy;
+                s1[i] += (double)dy * xh;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        sh[0][row][lane8 * 8 + i] = s0[i];
+        sh[1][row][lane8 * 8 + i] = s1[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * CH) {
+        const int k = threadIdx.x >> 6, c = threadIdx.x & 63;
+        double s = 0.0;
+        for (int r = 0; r < 32; ++r) s += sh[k][r][c];
+        part[((size_t)blockIdx.x * 2 + k) * CH + c] = s;
+    }
+}
+
+// Sums the partials of channel_reduce_kernel in block order: out[2][64].
+__global__ void channel_finalize_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+    const int k = threadIdx.x >> 6, c = threadIdx.x & 63;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[((size_t)b * 2 + k) * CH + c];
+    out[k * CH + c] = s;
+}
+
+// Batch statistics (biased variance) and the running-statistics update
+// (momentum 0.1, unbiased variance) of one BatchNorm layer.
+__global__ void bn_stats_kernel(const double* __restrict__ sums, float* __restrict__ bnp, float* __restrict__ rmean,
+                                float* __restrict__ rvar, double P) {
+    const int c = threadIdx.x;
+    const double mean = sums[c] / P;
+    const double var = fmax(sums[CH + c] / P - mean * mean, 0.0);
+    bnp[c] = (float)mean;
+    bnp[CH + c] = (float)(1.0 / sqrt(var + (double)BN_EPS));
+    rmean[c] = (1.0f - BN_MOMENTUM) * rmean[c] + BN_MOMENTUM * (float)mean;
+    rvar[c] = (1.0f - BN_MOMENTUM) * rvar[c] + BN_MOMENTUM * (float)(var * P / (P > 1 ? P - 1 : 1));
+}
+
+// a = relu(gamma (z - mean) istd + beta)
+__global__ void bn_apply_relu_kernel(const float* __restrict__ z, uint4* __restrict__ a, const float* __restrict__ bnp,
+                                     const float* __restrict__ gamma, const float* __restrict__ beta, size_t n8) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
+        const int c0 = (int)(i & 7) * 8;
+        float v[8];
+        f32x8_load(z + i * 8, v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = fmaxf(gamma[c0 + k] * (v[k] - bnp[c0 + k]) * bnp[CH + c0 + k] + beta[c0 + k], 0.0f);
+        a[i] = f32_to_bf16x8(v);
+    }
+}
+
+// dz = gamma istd (dy - sum(dy)/P - xhat sum(dy xhat)/P), dy = g [y > 0].
+__global__ void bn_bwd_apply_kernel(const uint4* __restrict__ g, const float* __restrict__ z, uint4* __restrict__ dz,
+                                    const float* __restrict__ bnp, const float* __restrict__ gamma,
+                                    const float* __restrict__ beta, const double* __restrict__ sums, double P,
+                                    size_t n8) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
+        const int c0 = (int)(i & 7) * 8;
+        float gv[8], zv[8], o[8];
+        bf16x8_to_f32(g[i], gv);
+        f32x8_load(z + i * 8, zv);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int c = c0 + k;
+            const float xh = (zv[k] - bnp[c]) * bnp[CH + c];
+            const float dy = (gamma[c] * xh + beta[c] > 0.0f) ? gv[k] : 0.0f;
+            const float m1 = (float)(sums[c] / P), m2 = (float)(sums[CH + c] / P);
+            o[k] = gamma[c] * bnp[CH + c] * (dy - m1 - xh * m2);
+        }
+        dz[i] = f32_to_bf16x8(o);
+    }
+}
+
+// dz = g * [a > 0] (layer 1: ReLU without BatchNorm)
+__global__ void relu_bwd_kernel(const uint4* __restrict__ g, const uint4* __restrict__ a, uint4* __restrict__ dz, size_t n8) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
+        float gv[8], av[8];
+        bf16x8_to_f32(g[i], gv);
+        bf16x8_to_f32(a[i], av);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gv[k] = av[k] > 0.0f ? gv[k] : 0.0f;
+        dz[i] = f32_to_bf16x8(gv);
+    }
+}
+
+// out = centre - R; loss partials of (out - clean)^2; dR = -2 (out - clean)/P.
+__global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ x, const float* __restrict__ clean,
+                                                   const float* __restrict__ R, float* __restrict__ dR, int B, int H,
+                                                   int W, double* __restrict__ part) {
+    const size_t P = (size_t)B * H * W, HW = (size_t)H * W;
+    const float scale = (float)(2.0 / (double)P);
+    double s = 0.0;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const size_t img = p / HW, r = p % HW;
+        const float centre = x[(img * FRAMES + 2) * HW + r];
+        const float d = centre - R[p] - clean[p];
+        dR[p] = -scale * d;
+        s += (double)d * d;
+    }
+    s = block_sum_f64(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void loss_finalize_kernel(const double* __restrict__ part, int n, double P, double* __restrict__ loss) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_sum_f64(s);
+    if (threadIdx.x == 0) *loss = s / P;
+}
+
+// Input gradient of the last layer (64 -> 1): da[p][ci] = sum_tap W[ci][tap] dR[p - off(tap)].
+__global__ void last_dgrad_kernel(const float* __restrict__ dR, const float* __restrict__ params, size_t w_off,
+                                  uint4* __restrict__ da, int B, int H, int W) {
+    __shared__ float w[CH * 9];
+    for (int i = threadIdx.x; i < CH * 9; i += blockDim.x) w[i] = params[w_off + i];   // [0][ci][ky][kx]
+    __syncthreads();
+    const size_t P = (size_t)B * H * W;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(p % W), a = (int)((p / W) % H);
+        const size_t base = p - (size_t)a * W - b;
+        float d[9];
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int aa = a - (tap / 3 - 1), bb = b - (tap % 3 - 1);
+            d[tap] = (aa >= 0 && aa < H && bb >= 0 && bb < W) ? dR[base + (size_t)aa * W + bb] : 0.0f;
+        }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+            float o[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                float s = 0.0f;
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) s += w[(c8 * 8 + k) * 9 + tap] * d[tap];
+                o[k] = s;
+            }
+            da[p * 8 + c8] = f32_to_bf16x8(o);
+        }
+    }
+}
+
+// Weight-gradient partials of a 64 -> 64 (TAPS = 9) or packed (TAPS = 1)
+// layer over one chunk of pixels:
+//   part[chunk][tap][co][ci] = sum_p dz[p][co] * act[p + off(tap)][ci]
+// 256 threads, each a 4 x 4 block of (co, ci); pixels staged 32 at a time.
+template <int TAPS>
+__global__ void __launch_bounds__(256) wgrad_kernel(const uint4* __restrict__ dz, const uint4* __restrict__ act,
+                                                    float* __restrict__ part, int B, int H, int W) {
+    __shared__ __align__(16) float sd[32][CH];
+    __shared__ __align__(16) float sa[32][CH];
+    const int tap = blockIdx.x, chunk = blockIdx.y;
+    const int dy = TAPS == 9 ? tap / 3 - 1 : 0, dx = TAPS == 9 ? tap % 3 - 1 : 0;
+    const size_t P = (size_t)B * H * W;
+    const size_t p_lo = (size_t)chunk * WG_CHUNK;
+    const size_t p_hi = p_lo + WG_CHUNK < P ? p_lo + WG_CHUNK : P;
+    const int co4 = (threadIdx.x >> 4) * 4, ci4 = (threadIdx.x & 15) * 4;
+    float acc[4][4] = {};
+    const int lr = threadIdx.x >> 3, lc = threadIdx.x & 7;     // loader: pixel row, 8-channel group
+    for (size_t p0 = p_lo; p0 < p_hi; p0 += 32) {
+        const size_t p = p0 + lr;
+        float v[8], u[8];
+        if (p < p_hi) {
+            bf16x8_to_f32(dz[p * 8 + lc], v);
+            const int b = (int)(p % W), a = (int)((p / W) % H);
+            const int aa = a + dy, bb = b + dx;
+            if (aa >= 0 && aa < H && bb >= 0 && bb < W) {
+                bf16x8_to_f32(act[(p + (ptrdiff_t)dy * W + dx) * 8 + lc], u);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) u[k] = 0.0f;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = u[k] = 0.0f;
+        }
+        *reinterpret_cast<float4*>(&sd[lr][lc * 8]) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(&sd[lr][lc * 8 + 4]) = make_float4(v[4], v[5], v[6], v[7]);
+        *reinterpret_cast<float4*>(&sa[lr][lc * 8]) = make_float4(u[0], u[1], u[2], u[3]);
+        *reinterpret_cast<float4*>(&sa[lr][lc * 8 + 4]) = make_float4(u[4], u[5], u[6], u[7]);
+        __syncthreads();
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const float4 d = *reinterpret_cast<const float4*>(&sd[j][co4]);
+            const float4 x = *reinterpret_cast<const float4*>(&sa[j][ci4]);
+            const float dd[4] = {d.x, d.y, d.z, d.w}, xx[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(dd[i], xx[k], acc[i][k]);
+        }
+        __syncthreads();
+    }
+    float* out = part + (((size_t)chunk * 9 + tap) * CH) * CH;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[(co4 + i) * CH + ci4 + k] = acc[i][k];
+}
+
+// Sums weight-gradient partials over chunks into the flat gradient layout.
+// layer 0: grad[w0 + co*45 + k] for k < 45; hidden: grad[w + (co*64 + ci)*9 + tap].
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int nchunks, int taps, int layer0,
+                                    float* __restrict__ grad) {
+    const int n = taps * CH * CH;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int tap = e / (CH * CH), co = (e / CH) % CH, ci = e % CH;
+        float s = 0.0f;
+        for (int c = 0; c < nchunks; ++c) s += part[((size_t)c * 9 + tap) * CH * CH + co * CH + ci];
+        if (layer0) {
+            if (ci < FRAMES * 9) grad[co * FRAMES * 9 + ci] = s;
+        } else {
+            grad[((size_t)co * CH + ci) * 9 + tap] = s;
+        }
+    }
+}
+
+// Last layer weight gradient: part[chunk][tap][ci] = sum_p dR[p] act[p + off(tap)][ci].
+__global__ void __launch_bounds__(256) wgrad_last_kernel(const float* __restrict__ dR, const uint4* __restrict__ act,
+                                                         float* __restrict__ part, int B, int H, int W) {
+    const int tap = blockIdx.x, chunk = blockIdx.y;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const size_t P = (size_t)B * H * W;
+    const size_t p_lo = (size_t)chunk * WG_CHUNK;
+    const size_t p_hi = p_lo + WG_CHUNK < P ? p_lo + WG_CHUNK : P;
+    const int lane8 = threadIdx.x & 7, row = threadIdx.x >> 3;    // 32 pixel rows x 8 channel groups
+    float acc[8] = {};
+    for (size_t p = p_lo + row; p < p_hi; p += 32) {
+        const int b = (int)(p % W), a = (int)((p / W) % H);
+        const int aa = a + dy, bb = b + dx;
+        if (aa < 0 || aa >= H || bb < 0 || bb >= W) continue;
+        float u[8];
+        bf16x8_to_f32(act[(p + (ptrdiff_t)dy * W + dx) * 8 + lane8], u);
+        const float d = dR[p];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = fmaf(d, u[k], acc[k]);
+    }
+    // reduce the 32 rows through shared memory
+    __shared__ float red[32][CH + 1];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[row][lane8 * 8 + k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < CH) {
+        float s = 0.0f;
+        for (int r = 0; r < 32; ++r) s += red[r][threadIdx.x];
+        part[((size_t)chunk * 9 + tap) * CH + threadIdx.x] = s;
+    }
+}
+
+__global__ void wgrad_last_reduce_kernel(const float* __restrict__ part, int nchunks, float* __restrict__ grad) {
+    const int e = threadIdx.x + blockIdx.x * blockDim.x;   // tap*64 + ci
+    if (e >= 9 * CH) return;
+    const int tap = e / CH, ci = e % CH;
+    float s = 0.0f;
+    for (int c = 0; c < nchunks; ++c) s += part[((size_t)c * 9 + tap) * CH + ci];
+    grad[ci * 9 + tap] = s;
+}
+
+__global__ void sum_f32_kernel(const float* __restrict__ x, size_t n, double* __restrict__ part) {
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) s += x[i];
+    s = block_sum_f64(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void store_sum_kernel(const double* __restrict__ part, int n, float* __restrict__ out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_sum_f64(s);
+    if (threadIdx.x == 0) *out = (float)s;
+}
+
+__global__ void copy_f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+// Adam (Kingma & Ba 2015) with bias correction: c1 = 1/(1-b1^t), c2 = 1/(1-b2^t).
+__global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, const uint8_t* __restrict__ frozen) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (frozen[i]) continue;
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        theta[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------- training pairs
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {   // SplitMix64 finaliser (Steele et al. 2014)
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float u01(uint64_t h) { return ((h >> 40) + 0.5f) * (1.0f / 16777216.0f); }
+
+// Patch p of the batch: a random frame of the phantom stack, a random slicing
+// axis (the 5 channels are 5 adjacent slices along it, standing in for time),
+// a random slice, a random 2D position, a random flip / transpose, and a noise
+// level sigma ~ U[lo, hi].  Noisy channels get independent N(0, sigma^2) noise
+// (Box-Muller on counter-based hashes); the target is the clean centre slice.
+__global__ void training_batch_kernel(const float* __restrict__ vol, int nx, int ny, int nz, int nframes, int B,
+                                      int Hp, int Wp, float s_lo, float s_hi, uint64_t seed, float* __restrict__ noisy,
+                                      float* __restrict__ clean) {
+    const size_t per = (size_t)FRAMES * Hp * Wp;
+    const size_t total = per * B;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int bi = (int)(e / per);
+        const int c = (int)((e / ((size_t)Hp * Wp)) % FRAMES);
+        const int i = (int)((e / Wp) % Hp), j = (int)(e % Wp);
+        const uint64_t h0 = mix64(seed ^ (0x1234567ull + (uint64_t)bi * 0x9E3779B97F4A7C15ull));
+        const uint64_t h1 = mix64(h0), h2 = mix64(h1), h3 = mix64(h2), h4 = mix64(h3), h5 = mix64(h4);
+        const int frame = (int)(u01(h0) * nframes) % nframes;
+        const int axis = (int)(u01(h1) * 3) % 3;           // 0: slices along z, 1: along x, 2: along y
+        const int flips = (int)(h2 & 7);
+        const float sigma = s_lo + (s_hi - s_lo) * u01(h5);
+        int S, A, Bd;                                       // slices, rows, cols of the chosen plane
+        if (axis == 0) { S = nz; A = ny; Bd = nx; } else if (axis == 1) { S = nx; A = nz; Bd = ny; } else { S = ny; A = nx; Bd = nz; }
+        const int s = (int)(u01(h3) * S) % S;
+        const int a0 = (int)(u01(h4) * (A - Hp + 1)) % (A - Hp + 1);
+        const int b0 = (int)(u01(mix64(h5)) * (Bd - Wp + 1)) % (Bd - Wp + 1);
+        int ii = i, jj = j;
+        if (flips & 1) ii = Hp - 1 - ii;
+        if (flips & 2) jj = Wp - 1 - jj;
+        if ((flips & 4) && Hp == Wp) { const int tt = ii; ii = jj; jj = tt; }
+        const int sc = min(max(s + c - 2, 0), S - 1);
+        const int a = a0 + ii, b = b0 + jj;
+        size_t idx;
+        if (axis == 0) idx = ((size_t)sc * ny + a) * nx + b;
+        else if (axis == 1) idx = ((size_t)a * ny + b) * nx + sc;
+        else idx = ((size_t)b * ny + sc) * nx + a;
+        const float v = vol[(size_t)frame * nx * ny * nz + idx];
+        const uint64_t hn = mix64(seed + 0xD1B54A32D192ED03ull * (e + 1));
+        const float u1 = u01(hn), u2 = u01(mix64(hn));
+        const float gauss = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        noisy[e] = v + sigma * gauss;
+        if (c == 2) clean[((size_t)bi * Hp + i) * Wp + j] = v;
+    }
+}
+
+}  // namespace cnn
+}  // namespace msf
+
+extern "C" msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels) {
+    MSF_REQUIRE(c, "msf_cnn_train_reserve: NULL handle");
+    MSF_REQUIRE(max_train_pixels >= 128, "msf_cnn_train_reserve: need at least 128 pixels");
+    if (max_train_pixels <= c->train_cap) return MSF_OK;
+    cudaFree(c->train_ws);
+    c->train_ws = nullptr;
+    c->train_cap = 0;
+    const size_t bytes = train_layout(max_train_pixels, nullptr, nullptr);
+    if (cudaMalloc(&c->train_ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MSF_ERR_NOMEM, "msf_cnn_train_reserve: cannot allocate %zu bytes", bytes);
+    }
+    c->train_ws_bytes = bytes;
+    c->train_cap = max_train_pixels;
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_cnn_get_grads(msf_cnn* c, float* h_grads, size_t n) {
+    MSF_REQUIRE(c && h_grads, "msf_cnn_get_grads: NULL argument");
+    MSF_REQUIRE(n == c->off.total, "msf_cnn_get_grads: expected %zu values, got %zu", c->off.total, n);
+    MSF_TRY_CUDA(cudaDeviceSynchronize());
+    MSF_TRY_CUDA(cudaMemcpy(h_grads, c->d_grad, n * 4, cudaMemcpyDeviceToHost));
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_training_batch(const float* d_vol, const msf_vol* vol, int B, int H, int W, double sigma_lo,
+                                         double sigma_hi, uint64_t seed, float* d_noisy, float* d_clean, void* stream) {
+    MSF_REQUIRE(d_vol && vol && d_noisy && d_clean, "msf_training_batch: NULL argument");
+    MSF_REQUIRE(B > 0 && H > 0 && W > 0, "msf_training_batch: empty batch");
+    MSF_REQUIRE(H <= vol->nx && H <= vol->ny && H <= vol->nz && W <= vol->nx && W <= vol->ny && W <= vol->nz,
+                "msf_training_batch: patch larger than the volume");
+    MSF_REQUIRE(sigma_lo >= 0 && sigma_hi >= sigma_lo, "msf_training_batch: need 0 <= sigma_lo <= sigma_hi");
+    cudaStream_t st = as_stream(stream);
+    MSF_PROF("training_batch", st);
+    training_batch_kernel<<<152 * 8, 256, 0, st>>>(d_vol, vol->nx, vol->ny, vol->nz, vol->nt, B, H, W, (float)sigma_lo,
+                                                   (float)sigma_hi, seed, d_noisy, d_clean);
+    MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const float* d_clean, int B, int H, int W,
+                                     float lr, float* h_loss, void* stream) {
+    MSF_REQUIRE(c && d_noisy && d_clean, "msf_train_step: NULL argument");
+    MSF_REQUIRE(B > 0 && H > 0 && W > 0, "msf_train_step: empty batch");
+    const int64_t P = (int64_t)B * H * W;
+    MSF_REQUIRE(P <= c->train_cap,
+                "msf_train_step: batch of %lld pixels exceeds the reserved training workspace (%lld); "
+                "call msf_cnn_train_reserve first", (long long)P, (long long)c->train_cap);
+    MSF_REQUIRE(lr > 0, "msf_train_step: lr must be positive");
+    cudaStream_t st = as_stream(stream);
+    TrainWS w;
+    train_layout(c->train_cap, &w, (uint8_t*)c->train_ws);
+    const Offsets& o = c->off;
+    const size_t n8 = (size_t)P * 8;
+    const int nchunks = (int)((P + WG_CHUNK - 1) / WG_CHUNK);
+
+    // weights of this step: forward (no folding) and input-gradient kernels
+    size_t wf_off[LAYERS], wp = 0;
+    for (int l = 0; l < LAYERS; ++l) { wf_off[l] = wp; wp += (size_t)taps_of(l) * rows_of(l) * KPACK; }
+    {
+        MSF_PROF("train_pack_weights", st);
+        for (int l = 0; l < LAYERS; ++l) {
+            FoldArgs f;
+            f.layer = l; f.taps = taps_of(l); f.rows = rows_of(l); f.cin = cin_of(l); f.cout = cout_of(l);
+            f.w = (long long)o.w[l]; f.b = (long long)o.b[l];
+            f.gamma = f.beta = f.mean = f.var = -1;
+            fold_kernel<<<64, 256, 0, st>>>(c->d_params, w.wf + wf_off[l], w.bf + l * CH, f);
+        }
+        pack_dgrad_kernel<<<256, 256, 0, st>>>(c->d_params, w.wb, o);
+        MSF_LAUNCH_CHECK();
+        MSF_TRY_CUDA(cudaMemsetAsync(w.zeros, 0, CH * 4, st));
+    }
+    CUtensorMap m16[LAYERS], m18[LAYERS], m4[LAYERS], g16[2], g18[2], g4[2], mw[LAYERS], mb[8];
+    for (int l = 0; l < LAYERS; ++l) {
+        MSF_TRY(make_act_map(&m16[l], w.act[l], B, H, W, TILE_A));
+        MSF_TRY(make_act_map(&m18[l], w.act[l], B, H, W, TILE_A + 2));
+        MSF_TRY(make_act_map(&m4[l], w.act[l], B, H, W, TILE_A / 4));
+        MSF_TRY(make_w_map(&mw[l], w.wf + wf_off[l], taps_of(l) * rows_of(l), rows_of(l)));
+    }
+    for (int k = 0; k < 2; ++k) {
+        MSF_TRY(make_act_map(&g16[k], w.g[k], B, H, W, TILE_A));
+        MSF_TRY(make_act_map(&g18[k], w.g[k], B, H, W, TILE_A + 2));
+        MSF_TRY(make_act_map(&g4[k], w.g[k], B, H, W, TILE_A / 4));
+    }
+    for (int l = 0; l < 8; ++l) MSF_TRY(make_w_map(&mb[l], w.wb + (size_t)l * 9 * CH * CH, 9 * CH, CH));
+    TileGeom tg;
+    tg.H = H; tg.W = W; tg.imgs = B;
+    tg.tiles_a = (H + TILE_A - 1) / TILE_A;
+    tg.tiles_b = (W + TILE_B - 1) / TILE_B;
+    tg.total = B * tg.tiles_a * tg.tiles_b;
+    SliceGeom sg{};
+    const int nred = w.nred;
+    auto reduce = [&](int mode, const void* t0, const float* t1, const float* bnp, const float* ga,
+                      const float* be, double* out) -> msf_status {
+        MSF_PROF("train_reduce", st);
+        if (mode == RED_MOMENTS)
+            channel_reduce_kernel<RED_MOMENTS><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+        else if (mode == RED_BNBWD)
+            channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+        else
+            channel_reduce_kernel<RED_SUM><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+        channel_finalize_kernel<<<1, 128, 0, st>>>(w.part, nred, out);
+        MSF_LAUNCH_CHECK();
+        return MSF_OK;
+    };
+
+    // ---------------- forward
+    {
+        MSF_PROF("train_pack_input", st);
+        pack_batch_kernel<<<152 * 8, 256, 0, st>>>(d_noisy, (uint4*)w.act[0], B, H, W);
+        MSF_LAUNCH_CHECK();
+    }
+    MSF_TRY((launch_conv<1, 64, 4, EPI_RELU>(m16[0], mw[0], m4[1], w.bf, tg, sg, nullptr, nullptr, c->d_err, st)));
+    for (int l = 1; l <= 8; ++l) {
+        MSF_TRY((launch_conv<9, 64, 2, EPI_RAW32>(m18[l], mw[l], m4[l], w.bf + l * CH, tg, sg, nullptr, w.z[l], c->d_err, st)));
+        double* sums = w.sums + (size_t)(l - 1) * 4 * CH;
+        float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
+        MSF_TRY(reduce(RED_MOMENTS, w.z[l], nullptr, nullptr, nullptr, nullptr, sums));
+        {
+            MSF_PROF("train_bn", st);
+            bn_stats_kernel<<<1, CH, 0, st>>>(sums, bnp, c->d_params + o.mean[l], c->d_params + o.var[l], (double)P);
+            bn_apply_relu_kernel<<<152 * 8, 256, 0, st>>>(w.z[l], (uint4*)w.act[l + 1], bnp,
+                                                          c->d_params + o.gamma[l], c->d_params + o.beta[l], n8);
+            MSF_LAUNCH_CHECK();
+        }
+    }
+    MSF_TRY((launch_conv<9, 16, 2, EPI_F32>(m18[9], mw[9], m4[9], w.bf + 9 * CH, tg, sg, nullptr, w.R, c->d_err, st)));
+    {
+        MSF_PROF("train_loss", st);
+        loss_kernel<<<nred, 256, 0, st>>>(d_noisy, d_clean, w.R, w.dR, B, H, W, w.part);
+        loss_finalize_kernel<<<1, 256, 0, st>>>(w.part, nred, (double)P, w.loss);
+        MSF_LAUNCH_CHECK();
+    }
+    // ---------------- backward
+    {
+        MSF_PROF("train_last_bwd", st);
+        last_dgrad_kernel<<<152 * 8, 256, 0, st>>>(w.dR, c->d_params, o.w[9], (uint4*)w.g[0], B, H, W);
+        wgrad_last_kernel<<<dim3(9, nchunks), 256, 0, st>>>(w.dR, (const uint4*)w.act[9], w.wpart, B, H, W);
+        wgrad_last_reduce_kernel<<<(9 * CH + 255) / 256, 256, 0, st>>>(w.wpart, nchunks, c->d_grad + o.w[9]);
+        sum_f32_kernel<<<nred, 256, 0, st>>>(w.dR, (size_t)P, w.part);
+        store_sum_kernel<<<1, 256, 0, st>>>(w.part, nred, c->d_grad + o.b[9]);
+        MSF_LAUNCH_CHECK();
+    }
+    int cur = 0;   // w.g[cur] holds the gradient w.r.t. act[l + 1]
+    for (int l = 8; l >= 1; --l) {
+        double* sums = w.sums + (size_t)(l - 1) * 4 * CH;
+        float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
+        const float* ga = c->d_params + o.gamma[l];
+        const float* be = c->d_params + o.beta[l];
+        MSF_TRY(reduce(RED_BNBWD, w.g[cur], w.z[l], bnp, ga, be, sums + 2 * CH));
+        {
+            MSF_PROF("train_bn_bwd", st);
+            // d gamma = sum dy xhat, d beta = sum dy
+            copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums + 3 * CH, c->d_grad + o.gamma[l], CH);
+            copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums + 2 * CH, c->d_grad + o.beta[l], CH);
+            bn_bwd_apply_kernel<<<152 * 8, 256, 0, st>>>((const uint4*)w.g[cur], w.z[l],
+                                                         (uint4*)w.g[cur ^ 1], bnp, ga, be, sums + 2 * CH, (double)P, n8);
+            MSF_LAUNCH_CHECK();
+        }
+        // dz in g[cur ^ 1]: conv bias grad, weight grad, input grad
+        MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, sums));
+        {
+            MSF_PROF("train_wgrad", st);
+            copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums, c->d_grad + o.b[l], CH);
+            wgrad_kernel<9><<<dim3(9, nchunks), 256, 0, st>>>((const uint4*)w.g[cur ^ 1], (const uint4*)w.act[l],
+                                                               w.wpart, B, H, W);
+            wgrad_reduce_kernel<<<144, 256, 0, st>>>(w.wpart, nchunks, 9, 0, c->d_grad + o.w[l]);
+            MSF_LAUNCH_CHECK();
+        }
+        MSF_TRY((launch_conv<9, 64, 2, EPI_RAW>(g18[cur ^ 1], mb[l - 1], g4[cur], w.zeros, tg, sg, nullptr, nullptr,
+                                               c->d_err, st)));
+        // g[cur] now holds the gradient w.r.t. act[l]
+    }
+    {
+        MSF_PROF("train_first_bwd", st);
+        relu_bwd_kernel<<<152 * 8, 256, 0, st>>>((const uint4*)w.g[cur], (const uint4*)w.act[1], (uint4*)w.g[cur ^ 1], n8);
+        MSF_LAUNCH_CHECK();
+    }
+    MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, w.sums));
+    {
+        MSF_PROF("train_wgrad", st);
+        copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(w.sums, c->d_grad + o.b[0], CH);
+        wgrad_kernel<1><<<dim3(1, nchunks), 256, 0, st>>>((const uint4*)w.g[cur ^ 1], (const uint4*)w.act[0], w.wpart,
+                                                           B, H, W);
+        wgrad_reduce_kernel<<<16, 256, 0, st>>>(w.wpart, nchunks, 1, 1, c->d_grad + o.w[0]);
+        MSF_LAUNCH_CHECK();
+    }
+    // ---------------- Adam on everything except the running statistics
+    c->adam_t += 1;
+    const double c1 = 1.0 / (1.0 - pow(0.9, (double)c->adam_t));
+    const double c2 = 1.0 / (1.0 - pow(0.999, (double)c->adam_t));
+    {
+        MSF_PROF("train_adam", st);
+        adam_kernel<<<152 * 4, 256, 0, st>>>(c->d_params, c->d_grad, c->d_m, c->d_v, o.total, lr, 0.9f, 0.999f, 1e-8f,
+                                             (float)c1, (float)c2, c->d_frozen);
+        MSF_LAUNCH_CHECK();
+    }
+    c->folded = false;
+    if (h_loss) {
+        double l = 0.0;
+        MSF_TRY_CUDA(cudaMemcpyAsync(&l, w.loss, 8, cudaMemcpyDeviceToHost, st));
+        MSF_TRY_CUDA(cudaStreamSynchronize(st));
+        int herr = 0;
+        MSF_TRY_CUDA(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) return fail((msf_status)herr, "msf_train_step: a device-side wait timed out");
+        if (!isfinite(l)) return fail(MSF_ERR_NUMERIC, "msf_train_step: non-finite loss");
+        *h_loss = (float)l;
+    }
+    return MSF_OK;
 }

@@ -82,6 +82,9 @@ _SIGS = {
     "msf_cnn_get_params": (_I, [_P, _P, _Z]),
     "msf_denoise": (_I, [_P, _I, ctypes.POINTER(msf_vol), _P, _P, _P]),
     "msf_train_step": (_I, [_P, _P, _P, _I, _I, _I, _F, ctypes.POINTER(_F), _P]),
+    "msf_cnn_train_reserve": (_I, [_P, ctypes.c_int64]),
+    "msf_cnn_get_grads": (_I, [_P, _P, _Z]),
+    "msf_training_batch": (_I, [_P, ctypes.POINTER(msf_vol), _I, _I, _I, _D, _D, ctypes.c_uint64, _P, _P, _P]),
     "msf_mace_create": (_I, [ctypes.POINTER(msf_mace_desc), ctypes.POINTER(_P)]),
     "msf_mace_destroy": (None, [_P]),
     "msf_mace_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
@@ -261,6 +264,21 @@ class Cnn:
         a = np.zeros(self.param_count(), dtype=np.float32)
         _check(lib().msf_cnn_get_params(self.handle, a.ctypes.data, a.size))
         return a
+
+    def get_grads(self) -> np.ndarray:
+        a = np.zeros(self.param_count(), dtype=np.float32)
+        _check(lib().msf_cnn_get_grads(self.handle, a.ctypes.data, a.size))
+        return a
+
+    def train_reserve(self, pixels: int):
+        _check(lib().msf_cnn_train_reserve(self.handle, int(pixels)))
+
+
+def msf_training_batch(vol_stack, vol: msf_vol, B: int, H: int, W: int, sigma_lo: float, sigma_hi: float,
+                       seed: int, noisy, clean, stream=None):
+    _check(lib().msf_training_batch(_f32(vol_stack), ctypes.byref(vol), B, H, W, sigma_lo, sigma_hi,
+                                    ctypes.c_uint64(seed & (2 ** 64 - 1)), _f32(noisy), _f32(clean),
+                                    _stream(stream)))
 
 
 def msf_denoise(cnn: Cnn, orient: int, vol: msf_vol, x, out, stream=None):

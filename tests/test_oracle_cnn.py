@@ -139,3 +139,30 @@ def test_agents_share_one_model_across_planes(oracle):
     vp = v.transpose(0, 3, 1, 2)
     b = oracle.denoise(np.ascontiguousarray(vp), layers, "xy").transpose(0, 2, 3, 1)
     np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-13)
+
+
+def test_bf16_emulation_modes(oracle):
+    # (i) a net without hidden BatchNorm layers (conv -> ReLU -> conv) on
+    # BF16-exact data with power-of-two weights keeps every forward value
+    # representable, so the emulating forward equals the exact one; its
+    # gradients pass through at most two roundings of 2^-9 each.
+    convs = [(np.zeros((64, 5, 3, 3)), np.zeros(64)), (np.zeros((1, 64, 3, 3)), np.zeros(1))]
+    convs[0][0][0, 2, 1, 1] = 0.5
+    convs[1][0][0, 0, 1, 1] = 0.25
+    x = oracle.bf16(synth.uniform(18, (2, 5, 6, 6)))
+    clean = oracle.bf16(synth.uniform(19, (2, 6, 6)))
+    l_e, g_e, _, _ = oracle.train_loss_grad(x, clean, convs, [], emulate_bf16=False)
+    l_b, g_b, _, _ = oracle.train_loss_grad(x, clean, convs, [], emulate_bf16=True)
+    assert l_b == l_e
+    for (a, _), (b, _) in zip(g_e, g_b):
+        # sums of products carrying two roundings each: norm-wise within 2^-7
+        assert np.linalg.norm(b - a) <= 2 ** -7 * np.linalg.norm(a)
+    # (ii) on a shallow, well-conditioned net the BF16 gradients stay within the
+    # BF16 error of the exact ones
+    convs, bns = synth.cnn_weights(20, channels=8, layers=3)
+    x = synth.uniform(21, (3, 5, 8, 8))
+    clean = synth.uniform(22, (3, 8, 8))
+    _, g_e, gb_e, _ = oracle.train_loss_grad(x, clean, convs, bns)
+    _, g_b, gb_b, _ = oracle.train_loss_grad(x, clean, convs, bns, emulate_bf16=True)
+    for (a, _), (b, _) in zip(g_e, g_b):
+        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(a)
