@@ -100,6 +100,14 @@ void msf_projector_destroy(msf_projector* p);
 /* Device bytes held by the plan. */
 size_t msf_projector_bytes(const msf_projector* p);
 
+/* Autotuner: times the forward projector with ray blocks of 32x4, 64x2 and
+ * 16x8 (columns x rows) and the gather adjoint with voxel runs of 8, 16 and 32
+ * along z on this plan's geometry, and keeps the fastest of each for the plan.
+ * Results do not depend on the choice (same per-ray arithmetic and the same
+ * per-voxel summation order).  Synchronises; allocates a temporary buffer.
+ * h_choice (optional, 3 ints) receives {block columns, block rows, z-run}. */
+msf_status msf_projector_autotune(msf_projector* p, void* stream, int* h_choice);
+
 /* y = A x for every time-point: the system matrix A_n of Sec. II, Eq. (2),
  * modelled as a Joseph ray-driven projector.  For each ray (one per detector
  * pixel and view) the major axis is x when |d_x| >= |d_y| else y; on every
@@ -273,6 +281,7 @@ typedef struct {
     double mu[4];     /* agent weights of the average, Eq. (9); sum to 1 */
     int n_cg;         /* CG iterations of the partial update L~ (Eq. (13)) */
     int n_sweeps;     /* ICD sweeps of the q-GGMRF agent per iteration */
+    int use_graph;    /* non-zero: run the iteration as a CUDA graph (see msf_mace_step) */
 } msf_mace_params;
 
 msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out);
@@ -281,8 +290,23 @@ void msf_mace_destroy(msf_mace* m);
 /* One pass of Algorithm 1:  X <- F~(W; X);  Z <- G(2X - W);  W <- W + 2 rho (Z - X).
  * X_0 <- L~(W_0; X_0) (warm-started CG), X_k <- H_k(W_k); the average of Eq. (9)
  * uses mu.  h_residual (optional, synchronises) receives the FP64 consensus
- * spread sqrt(sum_i mu_i ||X_i - Xbar||^2) / ||Xbar|| of the new X. */
+ * spread sqrt(sum_i mu_i ||X_i - Xbar||^2) / ||Xbar|| of the new X.
+ * With prm->use_graph the whole iteration (every kernel and the residual copy)
+ * is captured once on an internal stream into a CUDA graph and replayed on
+ * `stream`; the graph is re-captured when the parameters or the CNN's weights
+ * change.  Results are identical to the eager path. */
 msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, double* h_residual, void* stream);
+
+/* A queue of independent (uneven) MACE problems advanced together: each
+ * problem runs on its own internal stream forked from the caller's stream and
+ * joined back, so small problems share the GPU; with use_graph set for every
+ * problem the whole batch iteration is one captured CUDA graph.  Problems must
+ * not share a projector plan or a CNN handle (their workspaces). */
+typedef struct msf_mace_batch msf_mace_batch;
+msf_status msf_mace_batch_create(msf_mace** problems, int n, msf_mace_batch** out);
+void msf_mace_batch_destroy(msf_mace_batch* b);
+/* prm: n parameter sets; h_residuals (optional, n values) synchronises. */
+msf_status msf_mace_batch_step(msf_mace_batch* b, const msf_mace_params* prm, double* h_residuals, void* stream);
 
 /* ------------------------------------------------------------ phantoms (test/bench data) */
 

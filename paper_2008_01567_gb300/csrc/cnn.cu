@@ -136,7 +136,16 @@ struct SliceGeom {
     int nx, ny, nz, nt;
     int S, H, W;         // slices per frame, image rows, image cols
     int t0, nframes;     // frames of this chunk
+    long long ss, sa, sb;    // element strides of slice, row and column in a frame
 };
+
+// Strides of (slice, row, col) inside one [nz][ny][nx] frame for an orientation.
+static void set_strides(SliceGeom& g) {
+    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
+    if (g.orient == 0) { g.ss = sz; g.sa = sy; g.sb = sx; }        // s=z, a=y, b=x
+    else if (g.orient == 1) { g.ss = sx; g.sa = sz; g.sb = sy; }   // s=x, a=z, b=y
+    else { g.ss = sy; g.sa = sx; g.sb = sz; }                      // s=y, a=x, b=z
+}
 
 // 4D index of image pixel (a, b) of slice s at time-point t.
 __device__ __forceinline__ size_t vol_index(const SliceGeom& g, int t, int s, int a, int b) {
@@ -145,35 +154,60 @@ __device__ __forceinline__ size_t vol_index(const SliceGeom& g, int t, int s, in
     return (((size_t)t * g.nz + b) * g.ny + s) * g.nx + a;                          // s=y, a=x, b=z
 }
 
-// One thread per pixel of the chunk; the thread-to-pixel order follows the
-// volume's contiguous axis (x) so that the 45 gathers coalesce.
-__global__ void pack5_kernel(const float* __restrict__ vol, uint4* __restrict__ out, SliceGeom g) {
+// Frame [nz][ny][nx] -> the agent's [S][H][W] order, as a 2D transpose of
+// [rows][cols] -> [cols][rows] through 32 x 33 shared tiles: yz-t moves x to the
+// front (rows = nz*ny, cols = nx), zx-t moves z to the back (rows = nz, cols = ny*nx).
+__global__ void orient_transpose_kernel(const float* __restrict__ in, float* __restrict__ out, long long rows,
+                                        long long cols) {
+    __shared__ float tile[32][33];
+    const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const long long r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[k][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const long long c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+// One thread per pixel of the chunk, reading frames already in [S][H][W]
+// order (frames[c] points at time-point t0+tl+c-2, clamped, for tl = 0), so
+// consecutive threads read and write consecutive pixels of an image row.
+struct PackFrames {
+    const float* f[20];     // frame pointers for time-points first .. first+count-1
+    int first, count;
+};
+
+__global__ void pack5_kernel(PackFrames pf, uint4* __restrict__ out, SliceGeom g) {
     const size_t per_frame = (size_t)g.S * g.H * g.W;
     const size_t total = per_frame * g.nframes;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
         const int tl = (int)(p / per_frame);
-        size_t r = p % per_frame;
-        int s, a, b;
-        if (g.orient == 0) {          // b (= x) fastest
-            b = (int)(r % g.W); r /= g.W; a = (int)(r % g.H); s = (int)(r / g.H);
-        } else if (g.orient == 1) {   // s (= x) fastest
-            s = (int)(r % g.S); r /= g.S; b = (int)(r % g.W); a = (int)(r / g.W);
-        } else {                      // a (= x) fastest
-            a = (int)(r % g.H); r /= g.H; b = (int)(r % g.W); s = (int)(r / g.W);
-        }
+        const size_t r = p % per_frame;               // s*H*W + a*W + b
+        const int b = (int)(r % g.W), a = (int)((r / g.W) % g.H);
         const int t = g.t0 + tl;
+        const bool interior = a >= 1 && a <= g.H - 2 && b >= 1 && b <= g.W - 2;
         float v[FRAMES * 9];
 #pragma unroll
         for (int c = 0; c < FRAMES; ++c) {
             const int tc = min(max(t + c - 2, 0), g.nt - 1);
+            const float* f = pf.f[tc - pf.first] + r;
+            if (interior) {
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
+                for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const int aa = a + ky - 1, bb = b + kx - 1;
-                    v[c * 9 + ky * 3 + kx] =
-                        (aa >= 0 && aa < g.H && bb >= 0 && bb < g.W) ? __ldg(vol + vol_index(g, tc, s, aa, bb)) : 0.0f;
-                }
+                    for (int kx = 0; kx < 3; ++kx) v[c * 9 + ky * 3 + kx] = __ldg(f + (ky - 1) * g.W + (kx - 1));
+            } else {
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const int aa = a + ky - 1, bb = b + kx - 1;
+                        v[c * 9 + ky * 3 + kx] =
+                            (aa >= 0 && aa < g.H && bb >= 0 && bb < g.W) ? __ldg(f + (ky - 1) * g.W + (kx - 1)) : 0.0f;
+                    }
             }
         }
         uint32_t w[32];
@@ -184,8 +218,7 @@ __global__ void pack5_kernel(const float* __restrict__ vol, uint4* __restrict__ 
             __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
             w[i] = *reinterpret_cast<uint32_t*>(&h);
         }
-        const size_t img = (size_t)tl * g.S + s;
-        uint4* dst = out + ((img * g.H + a) * g.W + b) * 8;
+        uint4* dst = out + p * 8;    // [tl*S + s][a][b] is p itself
 #pragma unroll
         for (int c = 0; c < 8; ++c) dst[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
     }
@@ -211,7 +244,7 @@ struct ConvCfg {
     static constexpr int A_BYTES = TAPS == 9 ? 3 * HALO_BYTES : TILE_BYTES;
     static constexpr int W_BYTES = TAPS * N * 128;
     static constexpr int O_BYTES = epi_stores_bf16(EPI) ? 2 * TILE_BYTES : 0;
-    static constexpr int BAR_BYTES = 256;
+    static constexpr int BAR_BYTES = 512;   // barriers, TMEM slot, abort flag, bias
     static constexpr int SMEM = 1024 + NS * A_BYTES + W_BYTES + O_BYTES + BAR_BYTES;
 };
 
@@ -237,6 +270,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     uint64_t* wbar = tempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(wbar + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    float* sbias = (float*)((uint8_t*)bars + 256);
+    if (threadIdx.x < N) sbias[threadIdx.x] = bias[threadIdx.x];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -356,8 +391,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                 uint32_t w[N / 2];
 #pragma unroll
                 for (int j = 0; j < N / 2; ++j) {
-                    float lo = __uint_as_float(r[2 * j]) + __ldg(bias + 2 * j);
-                    float hi = __uint_as_float(r[2 * j + 1]) + __ldg(bias + 2 * j + 1);
+                    float lo = __uint_as_float(r[2 * j]) + sbias[2 * j];
+                    float hi = __uint_as_float(r[2 * j + 1]) + sbias[2 * j + 1];
                     if (EPI == EPI_RELU) {
                         lo = fmaxf(lo, 0.0f);
                         hi = fmaxf(hi, 0.0f);
@@ -388,13 +423,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                     float4* dst = reinterpret_cast<float4*>(outv + (((size_t)img * tg.H + a) * tg.W + b) * N);
 #pragma unroll
                     for (int j = 0; j < N / 4; ++j)
-                        dst[j] = make_float4(__uint_as_float(r[4 * j]) + __ldg(bias + 4 * j),
-                                             __uint_as_float(r[4 * j + 1]) + __ldg(bias + 4 * j + 1),
-                                             __uint_as_float(r[4 * j + 2]) + __ldg(bias + 4 * j + 2),
-                                             __uint_as_float(r[4 * j + 3]) + __ldg(bias + 4 * j + 3));
+                        dst[j] = make_float4(__uint_as_float(r[4 * j]) + sbias[4 * j],
+                                             __uint_as_float(r[4 * j + 1]) + sbias[4 * j + 1],
+                                             __uint_as_float(r[4 * j + 2]) + sbias[4 * j + 2],
+                                             __uint_as_float(r[4 * j + 3]) + sbias[4 * j + 3]);
                 }
             } else {
-                const float R = __uint_as_float(r[0]) + __ldg(bias);
+                const float R = __uint_as_float(r[0]) + sbias[0];
                 const int a = a0 + row / TILE_B, b = b0 + row % TILE_B;
                 if (a < tg.H && b < tg.W) {
                     if (EPI == EPI_RESID) {
@@ -414,6 +449,94 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- last layer (64 -> 1)
+
+__device__ __forceinline__ void bf16x8_lo(uint4 u, float* f) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        f[2 * i] = __uint_as_float(w[i] << 16);
+        f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+}
+
+// The last layer has one output channel: on the tensor cores it would cost
+// nearly a full 64-channel layer (operand reads dominate), so it runs on the
+// FP32 pipes.  A block stages a (16+2) x (32+2) halo tile of BF16 activations
+// in shared memory (16-byte chunk c of pixel p stored at chunk c ^ (p & 7), so
+// a warp reading one chunk of 32 neighbouring pixels touches all 32 banks);
+// each thread computes two vertically adjacent pixels and writes
+// centre - (R + bias) into the FP32 4D output in the agent's orientation.
+constexpr int L10_TA = 16, L10_TB = 32;
+constexpr int L10_ROWS = L10_TA + 2, L10_COLS = L10_TB + 2;
+constexpr int L10_SMEM = L10_ROWS * L10_COLS * 128;
+
+// Thread (slot, g): slot = threadIdx.x / 8 takes output pixels slot, slot+32,
+// ... of the 16 x 32 tile; g = threadIdx.x % 8 owns channels 8g..8g+7 and keeps
+// their 9 x 8 weights in registers.  The 8 partial sums of a pixel meet by
+// shuffles inside the 8 consecutive lanes.
+__global__ void __launch_bounds__(256, 2) last_layer_kernel(const uint4* __restrict__ act,
+                                                         const __nv_bfloat16* __restrict__ w16,
+                                                         const float* __restrict__ bias, TileGeom tg,
+                                                         SliceGeom sg, const float* __restrict__ centre,
+                                                         float* __restrict__ outv) {
+    extern __shared__ __align__(16) uint8_t l10_smem[];
+    uint4* tile = reinterpret_cast<uint4*>(l10_smem);
+    const int g = threadIdx.x & 7, slot = threadIdx.x >> 3;
+    float w[9][8];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[tap][k] = __bfloat162float(w16[(size_t)tap * 16 * CH + g * 8 + k]);
+    const int tiles_b = (tg.W + L10_TB - 1) / L10_TB, tiles_a = (tg.H + L10_TA - 1) / L10_TA;
+    const int per_img = tiles_a * tiles_b;
+    const float bv = bias[0];
+    for (int tile_id = blockIdx.x; tile_id < tg.imgs * per_img; tile_id += gridDim.x) {
+        const int img = tile_id / per_img;
+        const int r = tile_id % per_img;
+        const int a0 = (r / tiles_b) * L10_TA, b0 = (r % tiles_b) * L10_TB;
+        __syncthreads();
+        // every 16-byte copy of the tile in flight at once (cp.async); copies of
+        // the halo outside the image read nothing and zero-fill
+        for (int i = threadIdx.x; i < L10_ROWS * L10_COLS * 8; i += blockDim.x) {
+            const int p = i >> 3, c = i & 7;
+            const int aa = a0 - 1 + p / L10_COLS, bb = b0 - 1 + p % L10_COLS;
+            const bool in = aa >= 0 && aa < tg.H && bb >= 0 && bb < tg.W;
+            const uint4* src = in ? act + (((size_t)img * tg.H + aa) * tg.W + bb) * 8 + c : act;
+            const uint32_t dst = tc::smem_u32(&tile[p * 8 + (c ^ (p & 7))]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const int t = sg.t0 + img / sg.S, s = img % sg.S;
+#pragma unroll 4
+        for (int j = 0; j < (L10_TA * L10_TB) / 32; ++j) {   // 4 independent FMA chains in flight
+            const int po = slot + 32 * j;
+            const int ar = po / L10_TB, bc = po % L10_TB;
+            float acc = 0.0f;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int p = (ar + tap / 3) * L10_COLS + bc + tap % 3;
+                const uint4 u = tile[p * 8 + (g ^ (p & 7))];
+                float f[8];
+                bf16x8_lo(u, f);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc = fmaf(w[tap][k], f[k], acc);
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            const int a = a0 + ar, b = b0 + bc;
+            if (g == 0 && a < tg.H && b < tg.W) {
+                const size_t idx = vol_index(sg, t, s, a, b);
+                outv[idx] = centre[idx] - (acc + bv);
+            }
+        }
     }
 }
 
@@ -515,9 +638,11 @@ struct msf_cnn {
     float* d_bias = nullptr;        // [10][64]
     size_t wpack_off[LAYERS];
     __nv_bfloat16* d_act[2] = {nullptr, nullptr};
+    float* d_frames = nullptr;      // up to 5 * max_pixels floats: frames in the agent's [S][H][W] order
     int* d_err = nullptr;
     bool folded = false;
     int64_t adam_t = 0;
+    uint64_t gen = 1;               // bumped whenever the parameters change
     // training workspace (msf_cnn_train_reserve)
     int64_t train_cap = 0;
     void* train_ws = nullptr;
@@ -568,6 +693,7 @@ extern "C" msf_status msf_cnn_create(int64_t max_pixels, msf_cnn** out) {
               cudaMalloc(&c->d_m, P * 4) == cudaSuccess && cudaMalloc(&c->d_v, P * 4) == cudaSuccess &&
               cudaMalloc(&c->d_wpack, wp * 2) == cudaSuccess && cudaMalloc(&c->d_bias, LAYERS * CH * 4) == cudaSuccess &&
               cudaMalloc(&c->d_act[0], act) == cudaSuccess && cudaMalloc(&c->d_act[1], act) == cudaSuccess &&
+              cudaMalloc(&c->d_frames, (size_t)max_pixels * 5 * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess && cudaMalloc(&c->d_frozen, P) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -594,6 +720,7 @@ extern "C" void msf_cnn_destroy(msf_cnn* c) {
     cudaFree(c->d_params); cudaFree(c->d_grad); cudaFree(c->d_m); cudaFree(c->d_v);
     cudaFree(c->d_wpack); cudaFree(c->d_bias);
     cudaFree(c->d_act[0]); cudaFree(c->d_act[1]);
+    cudaFree(c->d_frames);
     cudaFree(c->d_err);
     cudaFree(c->d_frozen);
     cudaFree(c->train_ws);
@@ -607,6 +734,7 @@ extern "C" msf_status msf_cnn_set_params(msf_cnn* c, const float* h_params, size
     MSF_TRY_CUDA(cudaMemset(c->d_m, 0, n * 4));
     MSF_TRY_CUDA(cudaMemset(c->d_v, 0, n * 4));
     c->adam_t = 0;
+    c->gen += 1;
     MSF_TRY(fold_all(c, nullptr));
     MSF_TRY_CUDA(cudaDeviceSynchronize());
     return MSF_OK;
@@ -633,13 +761,14 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
     if (orient == MSF_XY_T) { sg.S = vol->nz; sg.H = vol->ny; sg.W = vol->nx; }
     else if (orient == MSF_YZ_T) { sg.S = vol->nx; sg.H = vol->nz; sg.W = vol->ny; }
     else { sg.S = vol->ny; sg.H = vol->nx; sg.W = vol->nz; }
+    set_strides(sg);
     const int64_t per_frame = (int64_t)sg.S * sg.H * sg.W;
     MSF_REQUIRE(per_frame <= c->max_pixels,
                 "msf_denoise: one time-point has %lld pixels but the handle holds %lld (max_pixels)",
                 (long long)per_frame, (long long)c->max_pixels);
     MSF_REQUIRE(per_frame * 128 < ((int64_t)1 << 40), "msf_denoise: frame too large");
     if (!c->folded) MSF_TRY(fold_all(c, st));
-    const int fchunk = (int)(c->max_pixels / per_frame);
+    const int fchunk = (int)(c->max_pixels / per_frame < 16 ? c->max_pixels / per_frame : 16);
     const int imgs_cap = fchunk * sg.S;
     CUtensorMap m16[2], m18[2], m4[2], mw[LAYERS];
     for (int b = 0; b < 2; ++b) {
@@ -653,8 +782,30 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
         sg.t0 = t0;
         sg.nframes = fchunk < vol->nt - t0 ? fchunk : vol->nt - t0;
         {
+            // the time-points this chunk reads, in the agent's [S][H][W] order
+            PackFrames pf;
+            pf.first = t0 - 2 > 0 ? t0 - 2 : 0;
+            const int last = t0 + sg.nframes + 1 < vol->nt - 1 ? t0 + sg.nframes + 1 : vol->nt - 1;
+            pf.count = last - pf.first + 1;
+            MSF_REQUIRE(pf.count <= 20 && (int64_t)pf.count * per_frame <= 5 * c->max_pixels,
+                        "msf_denoise: internal frame window too large");
+            for (int k = 0; k < pf.count; ++k) {
+                const float* src = d_in + (size_t)(pf.first + k) * per_frame;
+                if (orient == MSF_XY_T) {
+                    pf.f[k] = src;
+                } else {
+                    float* dst = c->d_frames + (size_t)k * per_frame;
+                    const long long rows = orient == MSF_YZ_T ? (long long)vol->nz * vol->ny : vol->nz;
+                    const long long cols = orient == MSF_YZ_T ? vol->nx : (long long)vol->ny * vol->nx;
+                    MSF_PROF("orient_transpose", st);
+                    orient_transpose_kernel<<<dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)),
+                                              dim3(32, 8), 0, st>>>(src, dst, rows, cols);
+                    MSF_LAUNCH_CHECK();
+                    pf.f[k] = dst;
+                }
+            }
             MSF_PROF("pack5", st);
-            pack5_kernel<<<152 * 16, 256, 0, st>>>(d_in, reinterpret_cast<uint4*>(c->d_act[0]), sg);
+            pack5_kernel<<<152 * 16, 256, 0, st>>>(pf, reinterpret_cast<uint4*>(c->d_act[0]), sg);
             MSF_LAUNCH_CHECK();
         }
         TileGeom tg;
@@ -671,8 +822,18 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
                                                     nullptr, nullptr, c->d_err, st)));
             cur ^= 1;
         }
-        MSF_TRY((launch_conv<9, 16, 2, EPI_RESID>(m18[cur], mw[LAYERS - 1], m4[cur ^ 1],
-                                                 c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out, c->d_err, st)));
+        {
+            MSF_PROF("last_layer", st);
+            static bool l10_attr = false;
+            if (!l10_attr) {
+                MSF_TRY_CUDA(cudaFuncSetAttribute(last_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L10_SMEM));
+                l10_attr = true;
+            }
+            last_layer_kernel<<<g_num_sms * 2, 256, L10_SMEM, st>>>(
+                reinterpret_cast<const uint4*>(c->d_act[cur]), c->d_wpack + c->wpack_off[LAYERS - 1],
+                c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out);
+            MSF_LAUNCH_CHECK();
+        }
     }
     return MSF_OK;
 }
@@ -1409,6 +1570,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         MSF_LAUNCH_CHECK();
     }
     c->folded = false;
+    c->gen += 1;
     if (h_loss) {
         double l = 0.0;
         MSF_TRY_CUDA(cudaMemcpyAsync(&l, w.loss, 8, cudaMemcpyDeviceToHost, st));
@@ -1419,5 +1581,27 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         if (!isfinite(l)) return fail(MSF_ERR_NUMERIC, "msf_train_step: non-finite loss");
         *h_loss = (float)l;
     }
+    return MSF_OK;
+}
+
+// ====================================================================== hooks for the MACE orchestration
+
+uint64_t msf::cnn_generation(const msf_cnn* c) { return c ? c->gen : 0; }
+
+// Everything msf_denoise does outside stream order, done ahead of a graph
+// capture: kernel attributes, the SM count, and the folding of the weights.
+msf_status msf::cnn_prepare(msf_cnn* c, cudaStream_t st) {
+    if (!c) return MSF_OK;
+    if (g_num_sms == 0) {
+        int dev = 0;
+        MSF_TRY_CUDA(cudaGetDevice(&dev));
+        MSF_TRY_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_tc_kernel<1, 64, 4, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      ConvCfg<1, 64, 4, EPI_RELU>::SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_tc_kernel<9, 64, 2, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      ConvCfg<9, 64, 2, EPI_RELU>::SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(last_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L10_SMEM));
+    if (!c->folded) MSF_TRY(fold_all(c, st));
     return MSF_OK;
 }

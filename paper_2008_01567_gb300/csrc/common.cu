@@ -88,6 +88,8 @@ static void prof_drain() {   // caller holds g_prof_mu
 
 ProfScope::ProfScope(const char* name, cudaStream_t stream) : stream_(stream) {
     if (!g_prof_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     int id = -1;
     for (size_t i = 0; i < g_prof_names.size(); ++i)

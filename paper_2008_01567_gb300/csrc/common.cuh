@@ -21,6 +21,11 @@ msf_status check_device();
 // The volume a projector plan was built for.
 const msf_vol* projector_volume(const msf_projector* p);
 
+// CNN handle state used by the MACE orchestration: a counter that changes with
+// the parameters, and the out-of-stream set-up done before a graph capture.
+uint64_t cnn_generation(const msf_cnn* c);
+msf_status cnn_prepare(msf_cnn* c, cudaStream_t st);
+
 }  // namespace msf
 
 #define MSF_TRY_CUDA(call)                                                                  \

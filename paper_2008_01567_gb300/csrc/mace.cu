@@ -5,8 +5,13 @@
 //   W <- W + 2 rho (Z - X)
 //
 // The consensus update is one pass over the K+1 stacked states that also forms
-// the FP64 partial sums of the consensus spread of X.
+// the FP64 partial sums of the consensus spread of X.  One iteration can be
+// captured once into a CUDA graph and replayed; a batch of independent
+// problems runs on forked streams inside one captured graph.
 #include <math.h>
+#include <string.h>
+
+#include <vector>
 
 #include "common.cuh"
 
@@ -15,9 +20,25 @@ struct msf_mace {
     msf_dataprox* dp = nullptr;
     double* d_partial = nullptr;   // [2][nblocks]
     double* d_sums = nullptr;      // [2]
-    double* h_sums = nullptr;      // pinned [2]
+    double* h_sums = nullptr;      // pinned [2], written by the step's last copy
     int nblocks = 0;
     size_t N = 0;                  // voxels of one 4D volume
+    // graph replay of one iteration
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    msf_mace_params gprm;
+    uint64_t gcnn = 0;
+};
+
+struct msf_mace_batch {
+    std::vector<msf_mace*> items;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<msf_mace_params> gprm;
+    std::vector<uint64_t> gcnn;
 };
 
 namespace msf {
@@ -79,6 +100,108 @@ __global__ void sum2_kernel(const double* __restrict__ partial, int n, double* _
     }
 }
 
+static msf_status check_params(const msf_mace* m, const msf_mace_params* prm) {
+    MSF_REQUIRE(prm->rho > 0 && prm->rho < 1, "msf_mace_step: rho must lie in (0,1) (Eq. (12))");
+    MSF_REQUIRE(prm->sigma > 0, "msf_mace_step: sigma must be positive");
+    const int K1 = m->desc.K + 1;
+    double musum = 0.0;
+    for (int i = 0; i < K1; ++i) {
+        MSF_REQUIRE(prm->mu[i] >= 0, "msf_mace_step: agent weights must be non-negative");
+        musum += prm->mu[i];
+    }
+    MSF_REQUIRE(fabs(musum - 1.0) < 1e-9, "msf_mace_step: agent weights must sum to 1 (got %.17g)", musum);
+    MSF_REQUIRE(prm->n_cg >= 0 && prm->n_sweeps >= 0, "msf_mace_step: iteration counts must be >= 0");
+    return MSF_OK;
+}
+
+// Enqueues one whole iteration on st, ending with the copy of the two FP64
+// residual sums into the handle's pinned buffer.
+static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStream_t st) {
+    const msf_mace_desc& d = m->desc;
+    const size_t N = m->N;
+    const int K1 = d.K + 1;
+    const msf_vol* vol = projector_volume(d.proj);
+    void* sv = reinterpret_cast<void*>(st);
+    // X_0 <- L~(W_0; X_0)
+    MSF_TRY(msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, sv));
+    // X_k <- H_k(W_k)
+    for (int k = 1; k < K1; ++k) {
+        if (d.prior == MSF_PRIOR_QGGMRF) {
+            MSF_TRY(msf_prox_qggmrf(vol, &d.mrf, d.d_W + k * N, d.d_X + k * N, prm->sigma, prm->n_sweeps, sv));
+        } else {
+            MSF_TRY(msf_denoise(d.cnn, (msf_orient)(k - 1), vol, d.d_W + k * N, d.d_X + k * N, sv));
+        }
+    }
+    // Z <- G(2X - W);  W <- W + 2 rho (Z - X)
+    MaceCoef c;
+    for (int i = 0; i < 4; ++i) c.mu[i] = i < K1 ? (float)prm->mu[i] : 0.0f;
+    c.two_rho = (float)(2.0 * prm->rho);
+    c.K1 = K1;
+    {
+        MSF_PROF("mace_consensus", st);
+        if (K1 == 2)
+            consensus_kernel<2><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
+        else
+            consensus_kernel<4><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
+        MSF_LAUNCH_CHECK();
+    }
+    {
+        MSF_PROF("mace_residual", st);
+        sum2_kernel<<<1, 1024, 0, st>>>(m->d_partial, m->nblocks, m->d_sums);
+        MSF_LAUNCH_CHECK();
+    }
+    MSF_TRY_CUDA(cudaMemcpyAsync(m->h_sums, m->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return MSF_OK;
+}
+
+static msf_status read_residual(const msf_mace* m, double* h_residual) {
+    const double num = m->h_sums[0], den = m->h_sums[1];
+    if (!isfinite(num) || !isfinite(den)) return fail(MSF_ERR_NUMERIC, "msf_mace_step: non-finite consensus residual");
+    *h_residual = den > 0 ? sqrt(num / den) : sqrt(num);
+    return MSF_OK;
+}
+
+static bool same_params(const msf_mace_params& a, const msf_mace_params& b) {
+    return a.rho == b.rho && a.sigma == b.sigma && memcmp(a.mu, b.mu, sizeof(a.mu)) == 0 && a.n_cg == b.n_cg &&
+           a.n_sweeps == b.n_sweeps;
+}
+
+static void drop_graph(cudaGraphExec_t& g) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+}
+
+// Captures `body` (enqueueing on the capture stream) into an executable graph.
+template <typename F>
+static msf_status capture(cudaStream_t cap, cudaGraphExec_t* out, F&& body) {
+    MSF_TRY_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    msf_status st = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (st != MSF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(MSF_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(MSF_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    return MSF_OK;
+}
+
+// Fork: every problem stream waits for `st`; each enqueues its iteration; join.
+static msf_status enqueue_batch(msf_mace_batch* b, const msf_mace_params* prm, cudaStream_t st) {
+    const int n = (int)b->items.size();
+    MSF_TRY_CUDA(cudaEventRecord(b->fork, st));
+    for (int i = 0; i < n; ++i) {
+        MSF_TRY_CUDA(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+        MSF_TRY(enqueue_step(b->items[i], &prm[i], b->streams[i]));
+        MSF_TRY_CUDA(cudaEventRecord(b->done[i], b->streams[i]));
+        MSF_TRY_CUDA(cudaStreamWaitEvent(st, b->done[i], 0));
+    }
+    return MSF_OK;
+}
+
 }  // namespace msf
 
 using namespace msf;
@@ -111,7 +234,8 @@ extern "C" msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out)
     m->nblocks = 152 * 8;
     if (cudaMalloc(&m->d_partial, 2 * m->nblocks * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->d_sums, 2 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&m->h_sums, 2 * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost(&m->h_sums, 2 * sizeof(double)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         msf_mace_destroy(m);
         return fail(MSF_ERR_NOMEM, "msf_mace_create: out of memory");
@@ -122,6 +246,8 @@ extern "C" msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out)
 
 extern "C" void msf_mace_destroy(msf_mace* m) {
     if (!m) return;
+    drop_graph(m->gexec);
+    if (m->cap) cudaStreamDestroy(m->cap);
     msf_dataprox_destroy(m->dp);
     cudaFree(m->d_partial);
     cudaFree(m->d_sums);
@@ -131,53 +257,100 @@ extern "C" void msf_mace_destroy(msf_mace* m) {
 
 extern "C" msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, double* h_residual, void* stream) {
     MSF_REQUIRE(m && prm, "msf_mace_step: NULL argument");
-    MSF_REQUIRE(prm->rho > 0 && prm->rho < 1, "msf_mace_step: rho must lie in (0,1) (Eq. (12))");
-    MSF_REQUIRE(prm->sigma > 0, "msf_mace_step: sigma must be positive");
-    const int K1 = m->desc.K + 1;
-    double musum = 0.0;
-    for (int i = 0; i < K1; ++i) {
-        MSF_REQUIRE(prm->mu[i] >= 0, "msf_mace_step: agent weights must be non-negative");
-        musum += prm->mu[i];
-    }
-    MSF_REQUIRE(fabs(musum - 1.0) < 1e-9, "msf_mace_step: agent weights must sum to 1 (got %.17g)", musum);
-    MSF_REQUIRE(prm->n_cg >= 0 && prm->n_sweeps >= 0, "msf_mace_step: iteration counts must be >= 0");
+    MSF_TRY(check_params(m, prm));
     cudaStream_t st = as_stream(stream);
-    const msf_mace_desc& d = m->desc;
-    const size_t N = m->N;
-    const msf_vol* vol = projector_volume(d.proj);
-    // X_0 <- L~(W_0; X_0)
-    MSF_TRY(msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, stream));
-    // X_k <- H_k(W_k)
-    for (int k = 1; k < K1; ++k) {
-        if (d.prior == MSF_PRIOR_QGGMRF) {
-            MSF_TRY(msf_prox_qggmrf(vol, &d.mrf, d.d_W + k * N, d.d_X + k * N, prm->sigma, prm->n_sweeps, stream));
-        } else {
-            MSF_TRY(msf_denoise(d.cnn, (msf_orient)(k - 1), vol, d.d_W + k * N, d.d_X + k * N, stream));
+    if (prm->use_graph) {
+        const uint64_t gen = cnn_generation(m->desc.cnn);
+        if (!m->gexec || !same_params(m->gprm, *prm) || m->gcnn != gen) {
+            drop_graph(m->gexec);
+            // work outside stream order first: kernel attributes, weight folding
+            MSF_TRY(cnn_prepare(m->desc.cnn, st));
+            MSF_TRY_CUDA(cudaStreamSynchronize(st));
+            MSF_TRY(capture(m->cap, &m->gexec, [&] { return enqueue_step(m, prm, m->cap); }));
+            m->gprm = *prm;
+            m->gcnn = gen;
         }
-    }
-    // Z <- G(2X - W);  W <- W + 2 rho (Z - X)
-    MaceCoef c;
-    for (int i = 0; i < 4; ++i) c.mu[i] = i < K1 ? (float)prm->mu[i] : 0.0f;
-    c.two_rho = (float)(2.0 * prm->rho);
-    c.K1 = K1;
-    MSF_PROF("mace_consensus", st);
-    if (K1 == 2)
-        consensus_kernel<2><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
-    else
-        consensus_kernel<4><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
-    MSF_LAUNCH_CHECK();
-    {
-        MSF_PROF("mace_residual", st);
-        sum2_kernel<<<1, 1024, 0, st>>>(m->d_partial, m->nblocks, m->d_sums);
-        MSF_LAUNCH_CHECK();
+        MSF_TRY_CUDA(cudaGraphLaunch(m->gexec, st));
+    } else {
+        MSF_TRY(enqueue_step(m, prm, st));
     }
     if (h_residual) {
-        MSF_TRY_CUDA(cudaMemcpyAsync(m->h_sums, m->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         MSF_TRY_CUDA(cudaStreamSynchronize(st));
-        const double num = m->h_sums[0], den = m->h_sums[1];
-        if (!isfinite(num) || !isfinite(den))
-            return fail(MSF_ERR_NUMERIC, "msf_mace_step: non-finite consensus residual");
-        *h_residual = den > 0 ? sqrt(num / den) : sqrt(num);
+        MSF_TRY(read_residual(m, h_residual));
+    }
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_mace_batch_create(msf_mace** problems, int n, msf_mace_batch** out) {
+    MSF_REQUIRE(problems && out && n > 0, "msf_mace_batch_create: need n > 0 problems");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        MSF_REQUIRE(problems[i], "msf_mace_batch_create: problem %d is NULL", i);
+        for (int j = 0; j < i; ++j) {
+            MSF_REQUIRE(problems[j] != problems[i], "msf_mace_batch_create: problem %d listed twice", i);
+            MSF_REQUIRE(!problems[i]->desc.cnn || problems[i]->desc.cnn != problems[j]->desc.cnn,
+                        "msf_mace_batch_create: problems %d and %d share a CNN handle (its workspace)", j, i);
+            MSF_REQUIRE(problems[i]->desc.proj != problems[j]->desc.proj,
+                        "msf_mace_batch_create: problems %d and %d share a projector plan (its workspace)", j, i);
+        }
+    }
+    msf_mace_batch* b = new msf_mace_batch();
+    b->items.assign(problems, problems + n);
+    b->streams.resize(n, nullptr);
+    b->done.resize(n, nullptr);
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < n; ++i)
+        ok = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        msf_mace_batch_destroy(b);
+        return fail(MSF_ERR_CUDA, "msf_mace_batch_create: cannot create streams");
+    }
+    *out = b;
+    return MSF_OK;
+}
+
+extern "C" void msf_mace_batch_destroy(msf_mace_batch* b) {
+    if (!b) return;
+    drop_graph(b->gexec);
+    for (cudaStream_t s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->done)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+extern "C" msf_status msf_mace_batch_step(msf_mace_batch* b, const msf_mace_params* prm, double* h_residuals,
+                                          void* stream) {
+    MSF_REQUIRE(b && prm, "msf_mace_batch_step: NULL argument");
+    const int n = (int)b->items.size();
+    for (int i = 0; i < n; ++i) MSF_TRY(check_params(b->items[i], &prm[i]));
+    cudaStream_t st = as_stream(stream);
+    bool graph = true;
+    for (int i = 0; i < n; ++i) graph = graph && prm[i].use_graph;
+    if (graph) {
+        bool fresh = b->gexec != nullptr && (int)b->gprm.size() == n;
+        for (int i = 0; fresh && i < n; ++i)
+            fresh = same_params(b->gprm[i], prm[i]) && b->gcnn[i] == cnn_generation(b->items[i]->desc.cnn);
+        if (!fresh) {
+            drop_graph(b->gexec);
+            for (int i = 0; i < n; ++i) MSF_TRY(cnn_prepare(b->items[i]->desc.cnn, st));
+            MSF_TRY_CUDA(cudaStreamSynchronize(st));
+            MSF_TRY(capture(b->cap, &b->gexec, [&] { return enqueue_batch(b, prm, b->cap); }));
+            b->gprm.assign(prm, prm + n);
+            b->gcnn.resize(n);
+            for (int i = 0; i < n; ++i) b->gcnn[i] = cnn_generation(b->items[i]->desc.cnn);
+        }
+        MSF_TRY_CUDA(cudaGraphLaunch(b->gexec, st));
+    } else {
+        MSF_TRY(enqueue_batch(b, prm, st));
+    }
+    if (h_residuals) {
+        MSF_TRY_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i) MSF_TRY(read_residual(b->items[i], &h_residuals[i]));
     }
     return MSF_OK;
 }

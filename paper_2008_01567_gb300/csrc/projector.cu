@@ -147,7 +147,8 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 
 enum FwdMode { FWD_PLAIN = 0, FWD_LAMBDA = 1, FWD_RESIDUAL = 2 };
 
-// One thread per ray; block = 32 columns x 4 rows of one view.  x-major rays
+// One thread per ray; a block covers blockDim.x columns x blockDim.y rows of one
+// view (128 threads; the shape is chosen per plan by msf_projector_autotune).  x-major rays
 // read the transposed frame [nz][nx][ny], y-major rays the natural frame
 // [nz][ny][nx], so in both cases the minor in-plane axis is contiguous.
 //   FWD_PLAIN:    out = A x
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     const float* __restrict__ x, const float* __restrict__ xT, const float4* __restrict__ col,
     float* __restrict__ out, const float* __restrict__ lam, const float* __restrict__ meas,
     ProjDims d) {
-    const int iu = blockIdx.x * 32 + threadIdx.x;
-    const int iv = blockIdx.y * 4 + threadIdx.y;
+    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
     const int g = blockIdx.z;
     if (iu >= d.nu || iv >= d.nv) return;
     const int t = g / d.views;
@@ -220,8 +221,8 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
 
 enum AdjMode { ADJ_PLAIN = 0, ADJ_CG_INIT = 1, ADJ_CG_Q = 2 };
 
-// Voxels of one z-run handled by one thread of the gather.
-constexpr int ADJ_ZB = 16;
+// Voxels of one z-run handled by one thread of the gather: 8, 16 or 32,
+// chosen per plan (default 16).
 
 // Detector u coordinate (in pixels) of the point (x, y, .) for view (cs, sn);
 // only used to bound candidate columns, so a fast division is enough.
@@ -232,8 +233,8 @@ __device__ __forceinline__ float u_pixel(float x, float y, float cs, float sn, c
 }
 
 // Adds, for the rays of one view whose major axis is XMAJ, w(ray, voxel) *
-// e'(ray) to the ADJ_ZB accumulators of the voxel run (ix, iy, iz_lo ..
-// iz_lo+ADJ_ZB-1), where e' = step * e is the step-weighted sinogram.
+// e'(ray) to the ZB accumulators of the voxel run (ix, iy, iz_lo ..
+// iz_lo+ZB-1), where e' = step * e is the step-weighted sinogram.
 //
 // An x-major ray touches column (ix, iy) on plane k = ix when floor(f_y) is
 // iy-1 or iy.  Candidate detector columns come from the exact projection of
@@ -244,7 +245,7 @@ __device__ __forceinline__ float u_pixel(float x, float y, float cs, float sn, c
 // its two z taps and its weights are those of the forward, bit for bit.
 // Every ray-plane crossing of the forward is visited by the two runs that hold
 // its a-taps, so the work tracks the forward's.
-template <bool XMAJ>
+template <bool XMAJ, int ZB>
 __device__ __forceinline__ void gather_runs(const float4* __restrict__ col, const float* __restrict__ e,
                                             int g, int ix, int iy, int iz_lo, float cs, float sn,
                                             const ProjDims& d, float (*acc)[128], int tid) {
@@ -273,11 +274,11 @@ __device__ __forceinline__ void gather_runs(const float4* __restrict__ col, cons
         if (ia != a0 && ia != a0 + 1) continue;
         const float wa1 = __fsub_rn(fa, a0f);
         const float wa = (ia == a0) ? __fsub_rn(1.0f, wa1) : wa1;
-        // rows with f_z in (iz_lo - 1, iz_lo + ADJ_ZB); gz > 0 (planes lie
+        // rows with f_z in (iz_lo - 1, iz_lo + ZB); gz > 0 (planes lie
         // between source and detector)
         const float rgz = __fdividef(1.0f, c.c1 + tk * c.inv_dmaj);
         const float va = (iz_lo - 1 - d.cz) * rgz * inv_dv + d.cv;
-        const float vb = (iz_lo + ADJ_ZB - d.cz) * rgz * inv_dv + d.cv;
+        const float vb = (iz_lo + ZB - d.cz) * rgz * inv_dv + d.cv;
         const int iv_lo = max(0, (int)floorf(va) - 1);
         const int iv_hi = min(d.nv - 1, (int)ceilf(vb) + 1);
         const float* erow = e + ((size_t)g * d.nv) * d.nu + iu;
@@ -286,48 +287,48 @@ __device__ __forceinline__ void gather_runs(const float4* __restrict__ col, cons
             const float fz = __fmaf_rn(tk, rz.bz, rz.fz_mid);
             const float z0f = floorf(fz);
             const int k0 = (int)z0f - iz_lo;
-            if (k0 < -1 || k0 >= ADJ_ZB) continue;
+            if (k0 < -1 || k0 >= ZB) continue;
             const float wz1 = __fsub_rn(fz, z0f);
             const float ev = wa * __ldg(erow + (size_t)iv * d.nu);
             if (k0 >= 0) acc[k0][tid] += __fsub_rn(1.0f, wz1) * ev;
-            if (k0 + 1 < ADJ_ZB) acc[k0 + 1][tid] += wz1 * ev;
+            if (k0 + 1 < ZB) acc[k0 + 1][tid] += wz1 * ev;
         }
     }
 }
 
-// One thread per run of ADJ_ZB voxels along z; block 32 (x) x 4 (y).
+// One thread per run of ZB voxels along z; block 32 (x) x 4 (y).
 // e is the step-weighted sinogram e' = step * e.
 //   ADJ_PLAIN:   out = A^T e
 //   ADJ_CG_INIT: r = A^T e + (v - z)/sigma^2, p = r, partial sum r.r
 //   ADJ_CG_Q:    q = A^T e + p/sigma^2, partial sum p.q
-template <int MODE>
+template <int MODE, int ZB>
 __global__ void __launch_bounds__(128) joseph_adj_kernel(
     const float4* __restrict__ col, const float2* __restrict__ trig, const int* __restrict__ vflag,
     const float* __restrict__ e, float* __restrict__ out, const float* __restrict__ a1,
     const float* __restrict__ a2, float* __restrict__ out2, double* __restrict__ partial,
     float inv_s2, ProjDims d) {
-    __shared__ float acc[ADJ_ZB][128];
+    __shared__ float acc[ZB][128];
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int ix = blockIdx.x * 32 + threadIdx.x;
     const int iy = blockIdx.y * 4 + threadIdx.y;
-    const int nzb = (d.nz + ADJ_ZB - 1) / ADJ_ZB;
+    const int nzb = (d.nz + ZB - 1) / ZB;
     const int zb = blockIdx.z % nzb;
     const int t = blockIdx.z / nzb;
-    const int iz_lo = zb * ADJ_ZB;
+    const int iz_lo = zb * ZB;
     const bool inside = ix < d.nx && iy < d.ny;
 #pragma unroll
-    for (int k = 0; k < ADJ_ZB; ++k) acc[k][tid] = 0.0f;
+    for (int k = 0; k < ZB; ++k) acc[k][tid] = 0.0f;
     if (inside) {
         for (int j = 0; j < d.views; ++j) {
             const int g = t * d.views + j;
             const float2 cs = __ldg(trig + g);
             const int fl = __ldg(vflag + g);
-            if (fl & 1) gather_runs<true>(col, e, g, ix, iy, iz_lo, cs.x, cs.y, d, acc, tid);
-            if (fl & 2) gather_runs<false>(col, e, g, ix, iy, iz_lo, cs.x, cs.y, d, acc, tid);
+            if (fl & 1) gather_runs<true, ZB>(col, e, g, ix, iy, iz_lo, cs.x, cs.y, d, acc, tid);
+            if (fl & 2) gather_runs<false, ZB>(col, e, g, ix, iy, iz_lo, cs.x, cs.y, d, acc, tid);
         }
     }
     double dot = 0.0;
-    for (int k = 0; k < ADJ_ZB; ++k) {
+    for (int k = 0; k < ZB; ++k) {
         const int iz = iz_lo + k;
         if (!inside || iz >= d.nz) break;
         const size_t i = (((size_t)t * d.nz + iz) * d.ny + iy) * d.nx + ix;
@@ -509,6 +510,8 @@ struct msf_projector {
     int* d_vflag = nullptr;
     float* d_xT = nullptr;
     float* d_sw = nullptr;     // step-weighted sinogram for msf_backproject
+    int fwd_bx = 32, fwd_by = 4;   // forward ray block (columns x rows)
+    int adj_zb = 16;               // gather z-run length
     size_t bytes = 0;
 };
 
@@ -542,8 +545,8 @@ static msf_status launch_fwd(msf_projector* p, int mode, const float* x, float* 
                              const float* lam, const float* meas, cudaStream_t st) {
     MSF_TRY(launch_transpose(p, x, p->d_xT, st));
     const ProjDims& d = p->dims;
-    dim3 grid((d.nu + 31) / 32, (d.nv + 3) / 4, d.nt * d.views);
-    dim3 block(32, 4);
+    dim3 block(p->fwd_bx, p->fwd_by);
+    dim3 grid((d.nu + block.x - 1) / block.x, (d.nv + block.y - 1) / block.y, d.nt * d.views);
     MSF_PROF("joseph_fwd", st);
     if (mode == FWD_PLAIN)
         joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
@@ -555,21 +558,37 @@ static msf_status launch_fwd(msf_projector* p, int mode, const float* x, float* 
     return MSF_OK;
 }
 
-static int adj_nzb(const ProjDims& d) { return (d.nz + ADJ_ZB - 1) / ADJ_ZB; }
-static dim3 adj_grid(const ProjDims& d) { return dim3((d.nx + 31) / 32, (d.ny + 3) / 4, adj_nzb(d) * d.nt); }
+static int adj_nzb(const ProjDims& d, int zb) { return (d.nz + zb - 1) / zb; }
+static dim3 adj_grid(const ProjDims& d, int zb) { return dim3((d.nx + 31) / 32, (d.ny + 3) / 4, adj_nzb(d, zb) * d.nt); }
+// partial sums per frame of an adjoint launch
+static int adj_parts(const msf_projector* p) {
+    const dim3 g = adj_grid(p->dims, p->adj_zb);
+    return g.x * g.y * adj_nzb(p->dims, p->adj_zb);
+}
+
+template <int MODE>
+static void launch_adj_zb(msf_projector* p, const float* e, float* out, const float* a1, const float* a2,
+                          float* out2, double* partial, float inv_s2, cudaStream_t st) {
+    const ProjDims& d = p->dims;
+    const dim3 block(32, 4), grid = adj_grid(d, p->adj_zb);
+    if (p->adj_zb == 8)
+        joseph_adj_kernel<MODE, 8><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
+    else if (p->adj_zb == 32)
+        joseph_adj_kernel<MODE, 32><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
+    else
+        joseph_adj_kernel<MODE, 16><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
+}
 
 static msf_status launch_adj(msf_projector* p, int mode, const float* e, float* out,
                              const float* a1, const float* a2, float* out2, double* partial,
                              float inv_s2, cudaStream_t st) {
-    const ProjDims& d = p->dims;
-    dim3 grid = adj_grid(d), block(32, 4);
     MSF_PROF("joseph_adj", st);
     if (mode == ADJ_PLAIN)
-        joseph_adj_kernel<ADJ_PLAIN><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
+        launch_adj_zb<ADJ_PLAIN>(p, e, out, a1, a2, out2, partial, inv_s2, st);
     else if (mode == ADJ_CG_INIT)
-        joseph_adj_kernel<ADJ_CG_INIT><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
+        launch_adj_zb<ADJ_CG_INIT>(p, e, out, a1, a2, out2, partial, inv_s2, st);
     else
-        joseph_adj_kernel<ADJ_CG_Q><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
+        launch_adj_zb<ADJ_CG_Q>(p, e, out, a1, a2, out2, partial, inv_s2, st);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
 }
@@ -688,8 +707,8 @@ extern "C" msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out) 
     msf_dataprox* d = new msf_dataprox();
     d->p = p;
     const size_t nv = vol_size(p->vol), ns = sino_size(p);
-    const dim3 ga = adj_grid(p->dims);
-    d->parts_adj = ga.x * ga.y * adj_nzb(p->dims);
+    const dim3 ga = adj_grid(p->dims, 8);             // the largest block count of any z-run
+    d->parts_adj = ga.x * ga.y * adj_nzb(p->dims, 8);
     d->parts_upd = 512;
     d->parts_max = d->parts_adj > d->parts_upd ? d->parts_adj : d->parts_upd;
     const int nt = p->vol.nt;
@@ -734,7 +753,7 @@ extern "C" msf_status msf_prox_data(msf_dataprox* dp, const float* d_y, const fl
     MSF_TRY(launch_adj(p, ADJ_CG_INIT, dp->d_s, dp->d_r, d_v, d_x, dp->d_p, dp->d_partial, inv_s2, st));
     {
         MSF_PROF("cg_finalize", st);
-        cg_finalize_kernel<FIN_RR0><<<nt, 256, 0, st>>>(dp->d_partial, dp->parts_adj, dp->d_rr, nullptr, dp->d_status);
+        cg_finalize_kernel<FIN_RR0><<<nt, 256, 0, st>>>(dp->d_partial, adj_parts(p), dp->d_rr, nullptr, dp->d_status);
         MSF_LAUNCH_CHECK();
     }
     const msf_vol& v = p->vol;
@@ -750,16 +769,17 @@ extern "C" msf_status msf_prox_data(msf_dataprox* dp, const float* d_y, const fl
         }
         {   // s = Lambda A p  (transpose already in p->d_xT)
             const ProjDims& d = p->dims;
-            dim3 grid((d.nu + 31) / 32, (d.nv + 3) / 4, d.nt * d.views);
+            dim3 block(p->fwd_bx, p->fwd_by);
+            dim3 grid((d.nu + block.x - 1) / block.x, (d.nv + block.y - 1) / block.y, d.nt * d.views);
             MSF_PROF("joseph_fwd", st);
-            joseph_fwd_kernel<FWD_LAMBDA><<<grid, dim3(32, 4), 0, st>>>(dp->d_p, p->d_xT, p->d_col, dp->d_s, d_lambda, nullptr, d);
+            joseph_fwd_kernel<FWD_LAMBDA><<<grid, block, 0, st>>>(dp->d_p, p->d_xT, p->d_col, dp->d_s, d_lambda, nullptr, d);
             MSF_LAUNCH_CHECK();
         }
         // q = A^T s + p/sigma^2 ; alpha = rr / p.q
         MSF_TRY(launch_adj(p, ADJ_CG_Q, dp->d_s, dp->d_q, dp->d_p, nullptr, nullptr, dp->d_partial, inv_s2, st));
         {
             MSF_PROF("cg_finalize", st);
-            cg_finalize_kernel<FIN_ALPHA><<<nt, 256, 0, st>>>(dp->d_partial, dp->parts_adj, dp->d_rr, dp->d_alpha, dp->d_status);
+            cg_finalize_kernel<FIN_ALPHA><<<nt, 256, 0, st>>>(dp->d_partial, adj_parts(p), dp->d_rr, dp->d_alpha, dp->d_status);
             MSF_LAUNCH_CHECK();
         }
         {   // z += alpha p ; r -= alpha q ; beta = r.r / rr
@@ -956,4 +976,67 @@ extern "C" msf_status msf_project_static(const msf_geom* geom, const msf_vol* vo
         MSF_LAUNCH_CHECK();
     }
     return MSF_OK;
+}
+
+// ====================================================================== autotuning
+
+extern "C" msf_status msf_projector_autotune(msf_projector* p, void* stream, int* h_choice) {
+    MSF_REQUIRE(p, "msf_projector_autotune: NULL plan");
+    cudaStream_t st = as_stream(stream);
+    const size_t nv = vol_size(p->vol), ns = sino_size(p);
+    // inputs: the plan's own scratch (transposed stack and step-weighted sinogram)
+    // are overwritten; outputs go to a temporary buffer allocated here
+    float* tmp = nullptr;
+    MSF_TRY_CUDA(cudaMalloc(&tmp, (nv > ns ? nv : ns) * sizeof(float)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    msf_status st_ = MSF_OK;
+    auto time_it = [&](auto&& fn) -> float {
+        fn();   // warm
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) fn();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    MSF_TRY_CUDA(cudaMemsetAsync(p->d_xT, 0, nv * sizeof(float), st));
+    MSF_TRY_CUDA(cudaMemsetAsync(p->d_sw, 0, ns * sizeof(float), st));
+    const int shapes[3][2] = {{32, 4}, {64, 2}, {16, 8}};
+    float best = 1e30f;
+    int bi = 0;
+    for (int i = 0; i < 3; ++i) {
+        p->fwd_bx = shapes[i][0];
+        p->fwd_by = shapes[i][1];
+        const float ms = time_it([&] {
+            const ProjDims& d = p->dims;
+            dim3 block(p->fwd_bx, p->fwd_by);
+            dim3 grid((d.nu + block.x - 1) / block.x, (d.nv + block.y - 1) / block.y, d.nt * d.views);
+            joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(p->d_xT, p->d_xT, p->d_col, tmp, nullptr, nullptr, d);
+        });
+        if (ms < best) { best = ms; bi = i; }
+    }
+    p->fwd_bx = shapes[bi][0];
+    p->fwd_by = shapes[bi][1];
+    const int zbs[3] = {8, 16, 32};
+    best = 1e30f;
+    int bz = 1;
+    for (int i = 0; i < 3; ++i) {
+        p->adj_zb = zbs[i];
+        const float ms = time_it([&] { launch_adj_zb<ADJ_PLAIN>(p, p->d_sw, tmp, nullptr, nullptr, nullptr, nullptr, 0.0f, st); });
+        if (ms < best) { best = ms; bz = i; }
+    }
+    p->adj_zb = zbs[bz];
+    if (cudaGetLastError() != cudaSuccess) st_ = fail(MSF_ERR_CUDA, "msf_projector_autotune: a trial launch failed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(tmp);
+    if (h_choice) {
+        h_choice[0] = p->fwd_bx;
+        h_choice[1] = p->fwd_by;
+        h_choice[2] = p->adj_zb;
+    }
+    return st_;
 }

@@ -52,7 +52,7 @@ class msf_mace_desc(ctypes.Structure):
 
 class msf_mace_params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("sigma", ctypes.c_double), ("mu", ctypes.c_double * 4),
-                ("n_cg", ctypes.c_int), ("n_sweeps", ctypes.c_int)]
+                ("n_cg", ctypes.c_int), ("n_sweeps", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -88,6 +88,10 @@ _SIGS = {
     "msf_mace_create": (_I, [ctypes.POINTER(msf_mace_desc), ctypes.POINTER(_P)]),
     "msf_mace_destroy": (None, [_P]),
     "msf_mace_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
+    "msf_mace_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    "msf_mace_batch_destroy": (None, [_P]),
+    "msf_mace_batch_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
+    "msf_projector_autotune": (_I, [_P, _P, ctypes.POINTER(_I)]),
     "msf_phantom_voxelize": (_I, [ctypes.POINTER(msf_vol), _P, _I, _I, _P, _P]),
     "msf_phantom_project": (_I, [_P, _P, _I, _P, _P]),
 }
@@ -351,13 +355,50 @@ class Mace:
     __del__ = close
 
 
+def mace_params(rho: float, sigma: float, mu, n_cg: int, n_sweeps: int = 0, use_graph: bool = False):
+    return msf_mace_params(rho, sigma, (ctypes.c_double * 4)(*(list(mu) + [0.0] * (4 - len(mu)))), n_cg, n_sweeps,
+                           1 if use_graph else 0)
+
+
 def msf_mace_step(m: Mace, rho: float, sigma: float, mu, n_cg: int, n_sweeps: int = 0, stream=None,
-                  want_residual: bool = True):
-    prm = msf_mace_params(rho, sigma, (ctypes.c_double * 4)(*(list(mu) + [0.0] * (4 - len(mu)))), n_cg, n_sweeps)
+                  want_residual: bool = True, use_graph: bool = False):
+    prm = mace_params(rho, sigma, mu, n_cg, n_sweeps, use_graph)
     r = ctypes.c_double(0.0)
     _check(lib().msf_mace_step(m.handle, ctypes.byref(prm), ctypes.byref(r) if want_residual else None,
                                _stream(stream)))
     return r.value if want_residual else None
+
+
+class MaceBatch:
+    """A queue of independent MACE problems advanced together (msf_mace_batch_*)."""
+
+    def __init__(self, maces):
+        arr = (ctypes.c_void_p * len(maces))(*[m.handle.value for m in maces])
+        h = ctypes.c_void_p()
+        _check(lib().msf_mace_batch_create(arr, len(maces), ctypes.byref(h)))
+        self.handle = h
+        self._keep = list(maces)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().msf_mace_batch_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def msf_mace_batch_step(b: MaceBatch, params, stream=None, want_residuals: bool = True):
+    n = len(b._keep)
+    arr = (msf_mace_params * n)(*params)
+    res = (ctypes.c_double * n)()
+    _check(lib().msf_mace_batch_step(b.handle, arr, res if want_residuals else None, _stream(stream)))
+    return list(res) if want_residuals else None
+
+
+def msf_projector_autotune(proj: Projector, stream=None):
+    choice = (ctypes.c_int * 3)()
+    _check(lib().msf_projector_autotune(proj.handle, _stream(stream), choice))
+    return tuple(choice)
 
 
 # ------------------------------------------------------------------ phantoms

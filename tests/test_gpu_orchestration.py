@@ -1,0 +1,117 @@
+"""Orchestration on the GPU, through the C ABI: a MACE iteration replayed as a
+CUDA graph, a batch of uneven problems in one captured graph, and the projector
+autotuner.  All three reorganise launches without changing any kernel's
+arithmetic or summation order, so they must reproduce the eager path bit for bit."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2008_01567_gb300 import synth
+from tests._problems import I0
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    from paper_2008_01567_gb300 import build, msf
+    build.build()
+    assert torch.cuda.is_available()
+    return msf
+
+
+def _problem(M, scan, seed, prior, cnn_params=None):
+    """Everything one MACE problem owns: plan, data, state, agents."""
+    import torch
+    P = M.Projector(scan)
+    ell = synth.ellipsoids(seed, 3, scan)
+    p = torch.empty((scan.nt, scan.views, scan.nv, scan.nu), device="cuda")
+    M.msf_phantom_project(P, ell, p)
+    counts = torch.from_numpy(synth.poisson(seed + 1, I0 * np.exp(-p.cpu().numpy().astype(np.float64)))
+                              .astype(np.float32)).cuda()
+    y, lam = torch.empty_like(counts), torch.empty_like(counts)
+    M.msf_weights(counts, y, lam, I0, I0)
+    K1 = 4 if prior == M.MSF_PRIOR_CNN else 2
+    W = torch.zeros((K1, scan.nt, scan.n, scan.n, scan.n), device="cuda")
+    X = torch.zeros_like(W)
+    cnn = None
+    if prior == M.MSF_PRIOR_CNN:
+        cnn = M.Cnn(scan.n ** 3)
+        cnn.set_params(cnn_params)
+        m = M.Mace(P, W, X, y, lam, prior, cnn=cnn)
+    else:
+        m = M.Mace(P, W, X, y, lam, prior, mrf=M.msf_mrf(2.0, 1.2, 1.0, 0.1, 0.5))
+    return dict(P=P, W=W, X=X, y=y, lam=lam, cnn=cnn, m=m, K1=K1)
+
+
+def _params(M, K1, rho=0.8, graph=False):
+    mu = [0.25] * 4 if K1 == 4 else [0.25, 0.75]
+    return M.mace_params(rho, 0.2, mu, 3, 1, graph)
+
+
+def test_graph_step_matches_eager(M):
+    import torch
+    flat = M.pack_params(*synth.cnn_weights(91))
+    scan = synth.Scan(n=20, nt=5, nu=28, nv=24, views=8)
+    a = _problem(M, scan, 92, M.MSF_PRIOR_CNN, flat)
+    b = _problem(M, scan, 92, M.MSF_PRIOR_CNN, flat)
+    for it in range(4):
+        rho = 0.8 if it < 2 else 0.6          # a parameter change forces a new capture
+        ra = M.msf_mace_step(a["m"], rho, 0.2, [0.25] * 4, 3)
+        rb = M.msf_mace_step(b["m"], rho, 0.2, [0.25] * 4, 3, use_graph=True)
+        assert ra == rb
+    torch.cuda.synchronize()
+    assert torch.equal(a["W"], b["W"]) and torch.equal(a["X"], b["X"])
+
+
+def test_batch_of_uneven_problems_matches_individual_steps(M):
+    import torch
+    flat = M.pack_params(*synth.cnn_weights(93))
+    scans = [synth.Scan(n=16, nt=4, nu=24, nv=24, views=6),
+             synth.Scan(n=24, nt=5, nu=36, nv=28, views=9, mode="wedge90"),
+             synth.Scan(n=32, nt=6, nu=44, nv=36, views=12)]
+    priors = [M.MSF_PRIOR_CNN, M.MSF_PRIOR_QGGMRF, M.MSF_PRIOR_CNN]
+    solo = [_problem(M, s, 94 + i, p, flat) for i, (s, p) in enumerate(zip(scans, priors))]
+    batch = [_problem(M, s, 94 + i, p, flat) for i, (s, p) in enumerate(zip(scans, priors))]
+    B = M.MaceBatch([q["m"] for q in batch])
+    for it in range(3):
+        res_solo = [M.msf_mace_step(q["m"], 0.8, 0.2, [0.25] * 4 if q["K1"] == 4 else [0.25, 0.75], 3, 1)
+                    for q in solo]
+        res_b = M.msf_mace_batch_step(B, [_params(M, q["K1"], graph=True) for q in batch])
+        assert res_solo == res_b
+    torch.cuda.synchronize()
+    for q, r in zip(solo, batch):
+        assert torch.equal(q["W"], r["W"]) and torch.equal(q["X"], r["X"])
+    # eager batch (no graph) gives the same answer too
+    res_e = M.msf_mace_batch_step(B, [_params(M, q["K1"], graph=False) for q in batch])
+    res_s = [M.msf_mace_step(q["m"], 0.8, 0.2, [0.25] * 4 if q["K1"] == 4 else [0.25, 0.75], 3, 1) for q in solo]
+    assert res_e == res_s
+
+
+def test_batch_rejects_shared_workspaces(M):
+    flat = M.pack_params(*synth.cnn_weights(95))
+    scan = synth.Scan(n=16, nt=4, nu=24, nv=24, views=6)
+    a = _problem(M, scan, 96, M.MSF_PRIOR_QGGMRF)
+    with pytest.raises(M.MsfError):
+        M.MaceBatch([a["m"], a["m"]])
+
+
+def test_autotune_keeps_results(M):
+    import torch
+    scan = dataclasses.replace(synth.PROJ, nt=2)
+    P = M.Projector(scan)
+    x = torch.empty((scan.nt, scan.n, scan.n, scan.n), device="cuda")
+    M.msf_phantom_voxelize(P.vol, synth.ellipsoids(97, 4, scan), x, ss=1)
+    e = torch.rand((scan.nt, scan.views, scan.nv, scan.nu), device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    y0, b0 = torch.empty_like(e), torch.empty_like(x)
+    M.msf_project(P, x, y0)
+    M.msf_backproject(P, e, b0)
+    choice = M.msf_projector_autotune(P)
+    assert choice[0] * choice[1] == 128 and choice[2] in (8, 16, 32)
+    y1, b1 = torch.empty_like(e), torch.empty_like(x)
+    M.msf_project(P, x, y1)
+    M.msf_backproject(P, e, b1)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1) and torch.equal(b0, b1)
