@@ -37,7 +37,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msf", choices=["msf", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "proj", "tiny"])
+    ap.add_argument("--workload", default="full", choices=["full", "proj", "tiny", "batch"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the short uneven-batch measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--iters", type=int, default=30, help="MACE iterations run for the NRMSE report")
@@ -47,7 +48,7 @@ def parse():
 
 def workload(name):
     from paper_2008_01567_gb300 import synth
-    return {"full": synth.FULL, "proj": synth.PROJ, "tiny": synth.TINY}[name]
+    return {"full": synth.FULL, "proj": synth.PROJ, "tiny": synth.TINY, "batch": synth.FULL}[name]
 
 
 # settings of the plain and learned runs (rho, sigma and agent weights of Eq. (9)).
@@ -143,10 +144,22 @@ def timed(fn, steps, warmup, dist):
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+        ms = max_over_ranks(ms, "cuda")
     return ms
+
+
+def max_over_ranks(value: float, device: str) -> float:
+    """The slowest rank's time: every rank solves its own problem, so the job
+    takes as long as its slowest replica."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.item()
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank reconstructs an independent problem (weak scaling, no data-path collective)."""
+    return 20200804 + 17 * rank
 
 
 # ---------------------------------------------------------------- algorithmic work per launch
@@ -268,6 +281,101 @@ def cpu_baseline(scan, settings, learned: bool):
             "ms_per_iter": T * 1e3}
 
 
+# ---------------------------------------------------------------- the queue of uneven problems
+
+def make_batch(params, seed, learned):
+    """The 12 uneven 4D problems (64^3x4 .. 192^3x12, 16..48 views, alternating
+    360 deg sparse and 90 deg wedge), each with its own plan, state and agents."""
+    import torch
+    from paper_2008_01567_gb300 import msf, synth
+    out = []
+    for i, sc in enumerate(synth.batch_scans()):
+        prob = make_problem(sc, seed + 31 * i)
+        msf.msf_projector_autotune(prob["P"])
+        K1 = 4 if learned else 2
+        W = torch.zeros((K1, sc.nt, sc.n, sc.n, sc.n), device="cuda")
+        X = torch.zeros_like(W)
+        if learned:
+            cnn = msf.Cnn(sc.n ** 3)
+            cnn.set_params(params)
+            m = msf.Mace(prob["P"], W, X, prob["y"], prob["lam"], msf.MSF_PRIOR_CNN, cnn=cnn)
+            prm = msf.mace_params(LEARNED["rho"], LEARNED["sigma"], LEARNED["mu"], LEARNED["n_cg"], 0, True)
+        else:
+            s = PLAIN
+            cnn = None
+            m = msf.Mace(prob["P"], W, X, prob["y"], prob["lam"], msf.MSF_PRIOR_QGGMRF,
+                         mrf=msf.msf_mrf(2.0, s["q"], s["T"], s["sx"], s["bt"]))
+            prm = msf.mace_params(s["rho"], s["sigma"], s["mu"], s["n_cg"], s["n_sweeps"], True)
+        out.append(dict(scan=sc, prob=prob, W=W, X=X, cnn=cnn, m=m, prm=prm))
+    return out
+
+
+def batch_throughput(params, seed, args, dist):
+    """Aggregate problem-iterations/s of the learned batch (one captured graph per iteration)."""
+    from paper_2008_01567_gb300 import msf
+    items = make_batch(params, seed + 1000, True)
+    B = msf.MaceBatch([it["m"] for it in items])
+    prms = [it["prm"] for it in items]
+    ms = timed(lambda: msf.msf_mace_batch_step(B, prms, want_residuals=False), max(1, args.steps), 2, dist)
+    n = len(items)
+    voxels = sum(it["scan"].nt * it["scan"].n ** 3 for it in items)
+    res = {"problems": n, "problem_iters_per_s": n * max(1, args.steps) / (ms / 1e3),
+           "batch_iters_per_s": max(1, args.steps) / (ms / 1e3), "voxels": voxels,
+           "ms_per_batch_iter": ms / max(1, args.steps)}
+    B.close()
+    return res
+
+
+def run_batch(args, rank, world, dist, seed):
+    """--workload batch: the 12 uneven problems, learned vs plain, NRMSE after
+    args.iters iterations and aggregate throughput."""
+    import torch
+    from paper_2008_01567_gb300 import msf, synth
+    tscan = synth.Scan(n=128, nt=4, nu=8, nv=8, views=1)
+    Pt = msf.Projector(tscan)
+    tvols = torch.empty((tscan.nt, tscan.n, tscan.n, tscan.n), device="cuda")
+    msf.msf_phantom_voxelize(Pt.vol, synth.ellipsoids(seed + 101, 10, tscan), tvols, ss=2)
+    cnn = msf.Cnn(128 ** 3)
+    cnn.set_params(msf.pack_params(*synth.cnn_weights(seed + 102)))
+    cnn.train_reserve(128 * 64 * 64)
+    tn = torch.empty((128, 5, 64, 64), device="cuda")
+    tc_ = torch.empty((128, 64, 64), device="cuda")
+    for it in range(args.train_steps):
+        msf.msf_training_batch(tvols, Pt.vol, 128, 64, 64, 0.02, 0.2, seed * 7919 + it, tn, tc_)
+        msf.msf_train_step(cnn, tn, tc_, 1e-3, want_loss=False)
+    params = cnn.get_params()
+    del tvols, tn, tc_, cnn
+    out = {}
+    for name, learned in (("learned", True), ("plain", False)):
+        items = make_batch(params, seed, learned)
+        B = msf.MaceBatch([it["m"] for it in items])
+        prms = [it["prm"] for it in items]
+        for _ in range(args.warmup):
+            msf.msf_mace_batch_step(B, prms, want_residuals=False)
+        ms = timed(lambda: msf.msf_mace_batch_step(B, prms, want_residuals=False), args.steps, 0, dist)
+        for _ in range(max(0, args.iters - args.warmup - args.steps)):
+            msf.msf_mace_batch_step(B, prms, want_residuals=False)
+        torch.cuda.synchronize()
+        nr = [(torch.linalg.vector_norm(it["X"][0] - it["prob"]["x_true"]) /
+               torch.linalg.vector_norm(it["prob"]["x_true"])).item() for it in items]
+        out[name] = {"problem_iters_per_s": world * len(items) * args.steps / (ms / 1e3),
+                     "ms_per_batch_iter": ms / args.steps, "nrmse": [round(x, 4) for x in nr]}
+        B.close()
+        del items
+    if rank == 0:
+        n = len(synth.batch_scans())
+        line = {"metric": METRIC, "value": out["learned"]["problem_iters_per_s"], "unit": "problem MACE iters/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": out["learned"]["ms_per_batch_iter"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 (CNN agents), f32 (projector, CG, consensus), f64 (scalars)",
+                "data": "synthetic (seeded moving-ellipsoid phantoms, Poisson 1e4)",
+                "config": {"workload": f"{n} uneven 4D problems 64^3x4..192^3x12, 16..48 views, 360/90 deg, "
+                                       "one captured graph per batch iteration"},
+                "learned": out["learned"], "plain": out["plain"]}
+        print(json.dumps(line))
+    return None
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -307,9 +415,12 @@ def main():
     from paper_2008_01567_gb300 import build, msf, synth
     build.build()
     peaks = load_peaks()
-    seed = 20200804 + 17 * rank
+    seed = replica_seed(rank)
+    if args.workload == "batch":
+        return run_batch(args, rank, world, dist, seed)
     prob = make_problem(scan, seed)
     P = prob["P"]
+    tuned = msf.msf_projector_autotune(P)
     N = scan.nt * scan.n ** 3
     total_iters = max(args.iters, args.warmup + args.steps)
 
@@ -380,8 +491,15 @@ def main():
         step()
         done += 1
     res = msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0)
-    learned = {"iters_per_s": value, "nrmse": nrmse(X[0]), "residual": res, "iters": done + 1}
+    # the same iteration replayed as one CUDA graph
+    gms = timed(lambda: msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0, want_residual=False,
+                                          use_graph=True), args.steps, 1, dist)
+    learned = {"iters_per_s": value, "graph_iters_per_s": world * args.steps / (gms / 1e3), "nrmse": nrmse(X[0]),
+               "residual": res, "iters": done + 1 + args.steps + 1}
     del m, W, X
+    batch = None
+    if not args.no_batch:
+        batch = batch_throughput(cnn.get_params(), seed, args, dist)
 
     # ---------------- plain q-GGMRF MACE at the same size
     s = PLAIN
@@ -441,6 +559,7 @@ def main():
                 "roofline": roofline(prof, scan, 4, peaks, args.steps),
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
                 "learned": learned, "plain": plain, "training": training, "projector": projector,
+                "projector_tuning": {"fwd_block": list(tuned[:2]), "adj_zrun": tuned[2]}, "batch": batch,
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()}}
         print(json.dumps(line))
     if dist:

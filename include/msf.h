@@ -64,6 +64,13 @@ void msf_profile_enable(int on);
 void msf_profile_reset(void);
 int msf_profile_read(int i, const char** name, int64_t* launches, double* total_ms);
 
+/* Failure-detection self-test (no counterpart in the paper): launches a kernel
+ * that waits, with the bounded wait every device-side wait of this library
+ * uses, on an mbarrier that nothing completes.  Returns MSF_ERR_TIMEOUT once
+ * the wait gives up after limit_ns (at most 2 s); the context stays usable.
+ * Synchronises.  Any other status means the bounded wait is broken. */
+msf_status msf_selftest_wait(uint64_t limit_ns, void* stream);
+
 /* ------------------------------------------------------------ problem data */
 
 /* One 4D volume: nt frames of nx*ny*nz isotropic voxels of edge `voxel`

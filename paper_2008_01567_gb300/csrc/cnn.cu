@@ -452,94 +452,6 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     }
 }
 
-// ---------------------------------------------------------------- last layer (64 -> 1)
-
-__device__ __forceinline__ void bf16x8_lo(uint4 u, float* f) {
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        f[2 * i] = __uint_as_float(w[i] << 16);
-        f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-    }
-}
-
-// The last layer has one output channel: on the tensor cores it would cost
-// nearly a full 64-channel layer (operand reads dominate), so it runs on the
-// FP32 pipes.  A block stages a (16+2) x (32+2) halo tile of BF16 activations
-// in shared memory (16-byte chunk c of pixel p stored at chunk c ^ (p & 7), so
-// a warp reading one chunk of 32 neighbouring pixels touches all 32 banks);
-// each thread computes two vertically adjacent pixels and writes
-// centre - (R + bias) into the FP32 4D output in the agent's orientation.
-constexpr int L10_TA = 16, L10_TB = 32;
-constexpr int L10_ROWS = L10_TA + 2, L10_COLS = L10_TB + 2;
-constexpr int L10_SMEM = L10_ROWS * L10_COLS * 128;
-
-// Thread (slot, g): slot = threadIdx.x / 8 takes output pixels slot, slot+32,
-// ... of the 16 x 32 tile; g = threadIdx.x % 8 owns channels 8g..8g+7 and keeps
-// their 9 x 8 weights in registers.  The 8 partial sums of a pixel meet by
-// shuffles inside the 8 consecutive lanes.
-__global__ void __launch_bounds__(256, 2) last_layer_kernel(const uint4* __restrict__ act,
-                                                         const __nv_bfloat16* __restrict__ w16,
-                                                         const float* __restrict__ bias, TileGeom tg,
-                                                         SliceGeom sg, const float* __restrict__ centre,
-                                                         float* __restrict__ outv) {
-    extern __shared__ __align__(16) uint8_t l10_smem[];
-    uint4* tile = reinterpret_cast<uint4*>(l10_smem);
-    const int g = threadIdx.x & 7, slot = threadIdx.x >> 3;
-    float w[9][8];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[tap][k] = __bfloat162float(w16[(size_t)tap * 16 * CH + g * 8 + k]);
-    const int tiles_b = (tg.W + L10_TB - 1) / L10_TB, tiles_a = (tg.H + L10_TA - 1) / L10_TA;
-    const int per_img = tiles_a * tiles_b;
-    const float bv = bias[0];
-    for (int tile_id = blockIdx.x; tile_id < tg.imgs * per_img; tile_id += gridDim.x) {
-        const int img = tile_id / per_img;
-        const int r = tile_id % per_img;
-        const int a0 = (r / tiles_b) * L10_TA, b0 = (r % tiles_b) * L10_TB;
-        __syncthreads();
-        // every 16-byte copy of the tile in flight at once (cp.async); copies of
-        // the halo outside the image read nothing and zero-fill
-        for (int i = threadIdx.x; i < L10_ROWS * L10_COLS * 8; i += blockDim.x) {
-            const int p = i >> 3, c = i & 7;
-            const int aa = a0 - 1 + p / L10_COLS, bb = b0 - 1 + p % L10_COLS;
-            const bool in = aa >= 0 && aa < tg.H && bb >= 0 && bb < tg.W;
-            const uint4* src = in ? act + (((size_t)img * tg.H + aa) * tg.W + bb) * 8 + c : act;
-            const uint32_t dst = tc::smem_u32(&tile[p * 8 + (c ^ (p & 7))]);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncthreads();
-        const int t = sg.t0 + img / sg.S, s = img % sg.S;
-#pragma unroll 4
-        for (int j = 0; j < (L10_TA * L10_TB) / 32; ++j) {   // 4 independent FMA chains in flight
-            const int po = slot + 32 * j;
-            const int ar = po / L10_TB, bc = po % L10_TB;
-            float acc = 0.0f;
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int p = (ar + tap / 3) * L10_COLS + bc + tap % 3;
-                const uint4 u = tile[p * 8 + (g ^ (p & 7))];
-                float f[8];
-                bf16x8_lo(u, f);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) acc = fmaf(w[tap][k], f[k], acc);
-            }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            const int a = a0 + ar, b = b0 + bc;
-            if (g == 0 && a < tg.H && b < tg.W) {
-                const size_t idx = vol_index(sg, t, s, a, b);
-                outv[idx] = centre[idx] - (acc + bv);
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------- host helpers
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -592,21 +504,37 @@ static msf_status make_w_map(CUtensorMap* m, void* base, int rows_total, int box
 static int g_num_sms = 0;
 
 template <int TAPS, int N, int NS, int EPI>
+static cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(conv_tc_kernel<TAPS, N, NS, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                ConvCfg<TAPS, N, NS, EPI>::SMEM);
+}
+
+// One-time, out-of-stream set-up of every conv variant (shared-memory limits)
+// and of the SM count; done before any launch so that no such call ever lands
+// inside a stream capture.
+static msf_status ensure_kernel_attrs() {
+    static bool done = false;
+    if (done) return MSF_OK;
+    int dev = 0;
+    MSF_TRY_CUDA(cudaGetDevice(&dev));
+    MSF_TRY_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    MSF_TRY_CUDA((set_smem_attr<1, 64, 4, EPI_RELU>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 64, 2, EPI_RELU>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 64, 2, EPI_RAW>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 64, 2, EPI_RAW32>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 16, 2, EPI_RESID>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 16, 2, EPI_F32>()));
+    done = true;
+    return MSF_OK;
+}
+
+template <int TAPS, int N, int NS, int EPI>
 static msf_status launch_conv(const CUtensorMap& ma, const CUtensorMap& mw, const CUtensorMap& mo, const float* bias,
                               const TileGeom& tg, const SliceGeom& sg, const float* centre, float* outv, int* err,
                               cudaStream_t st) {
     using C = ConvCfg<TAPS, N, NS, EPI>;
     auto kern = conv_tc_kernel<TAPS, N, NS, EPI>;
-    static bool attr = false;
-    if (!attr) {
-        MSF_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-        attr = true;
-    }
-    if (g_num_sms == 0) {
-        int dev = 0;
-        MSF_TRY_CUDA(cudaGetDevice(&dev));
-        MSF_TRY_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    }
+    MSF_TRY(ensure_kernel_attrs());
     const int grid = tg.total < g_num_sms ? tg.total : g_num_sms;
     if (grid <= 0) return MSF_OK;
     MSF_PROF(TAPS == 1 ? "conv1_tc"
@@ -679,6 +607,7 @@ extern "C" msf_status msf_cnn_create(int64_t max_pixels, msf_cnn** out) {
     *out = nullptr;
     MSF_REQUIRE(max_pixels >= 128, "msf_cnn_create: max_pixels must be >= 128");
     MSF_TRY(check_device());
+    MSF_TRY(ensure_kernel_attrs());
     msf_cnn* c = new msf_cnn();
     c->max_pixels = max_pixels;
     c->off = offsets();
@@ -822,18 +751,8 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
                                                     nullptr, nullptr, c->d_err, st)));
             cur ^= 1;
         }
-        {
-            MSF_PROF("last_layer", st);
-            static bool l10_attr = false;
-            if (!l10_attr) {
-                MSF_TRY_CUDA(cudaFuncSetAttribute(last_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L10_SMEM));
-                l10_attr = true;
-            }
-            last_layer_kernel<<<g_num_sms * 2, 256, L10_SMEM, st>>>(
-                reinterpret_cast<const uint4*>(c->d_act[cur]), c->d_wpack + c->wpack_off[LAYERS - 1],
-                c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out);
-            MSF_LAUNCH_CHECK();
-        }
+        MSF_TRY((launch_conv<9, 16, 2, EPI_RESID>(m18[cur], mw[LAYERS - 1], m4[cur ^ 1],
+                                                 c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out, c->d_err, st)));
     }
     return MSF_OK;
 }
@@ -1592,16 +1511,50 @@ uint64_t msf::cnn_generation(const msf_cnn* c) { return c ? c->gen : 0; }
 // capture: kernel attributes, the SM count, and the folding of the weights.
 msf_status msf::cnn_prepare(msf_cnn* c, cudaStream_t st) {
     if (!c) return MSF_OK;
-    if (g_num_sms == 0) {
-        int dev = 0;
-        MSF_TRY_CUDA(cudaGetDevice(&dev));
-        MSF_TRY_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    }
-    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_tc_kernel<1, 64, 4, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      ConvCfg<1, 64, 4, EPI_RELU>::SMEM));
-    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_tc_kernel<9, 64, 2, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      ConvCfg<9, 64, 2, EPI_RELU>::SMEM));
-    MSF_TRY_CUDA(cudaFuncSetAttribute(last_layer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, L10_SMEM));
+    MSF_TRY(ensure_kernel_attrs());
     if (!c->folded) MSF_TRY(fold_all(c, st));
     return MSF_OK;
+}
+
+// ====================================================================== failure detection self-test
+
+namespace msf {
+namespace cnn {
+// Waits on an mbarrier that nothing ever completes, with the same bounded wait
+// the conv kernels use; must give up after limit_ns and report a timeout.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int* status) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool ok = tc::mbar_wait(&bar, 0, &abort_flag, limit_ns);
+        *status = ok ? (int)MSF_OK : (int)MSF_ERR_TIMEOUT;
+    }
+}
+}  // namespace cnn
+}  // namespace msf
+
+extern "C" msf_status msf_selftest_wait(uint64_t limit_ns, void* stream) {
+    MSF_REQUIRE(limit_ns > 0 && limit_ns <= 2000000000ull, "msf_selftest_wait: limit must be in (0, 2 s]");
+    MSF_TRY(check_device());
+    cudaStream_t st = as_stream(stream);
+    int* d_status = nullptr;
+    int h = -1;
+    MSF_TRY_CUDA(cudaMalloc(&d_status, sizeof(int)));
+    cudaError_t e = cudaMemsetAsync(d_status, 0xff, sizeof(int), st);
+    if (e == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, d_status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_status);
+    if (e != cudaSuccess) return fail(MSF_ERR_CUDA, "msf_selftest_wait: %s", cudaGetErrorString(e));
+    if (h == (int)MSF_ERR_TIMEOUT) return fail(MSF_ERR_TIMEOUT, "msf_selftest_wait: the bounded wait gave up as designed");
+    return (msf_status)h;
 }

@@ -92,6 +92,7 @@ _SIGS = {
     "msf_mace_batch_destroy": (None, [_P]),
     "msf_mace_batch_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
     "msf_projector_autotune": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "msf_selftest_wait": (_I, [ctypes.c_uint64, _P]),
     "msf_phantom_voxelize": (_I, [ctypes.POINTER(msf_vol), _P, _I, _I, _P, _P]),
     "msf_phantom_project": (_I, [_P, _P, _I, _P, _P]),
 }
@@ -413,3 +414,8 @@ def msf_phantom_voxelize(vol: msf_vol, ell: np.ndarray, x, ss: int = 4, stream=N
 def msf_phantom_project(proj: Projector, ell: np.ndarray, y, stream=None):
     e = np.ascontiguousarray(ell, dtype=np.float64)
     _check(lib().msf_phantom_project(proj.handle, e.ctypes.data, e.shape[-2], _f32(y), _stream(stream)))
+
+
+def msf_selftest_wait(limit_ns: int, stream=None) -> int:
+    """Runs the bounded-wait self-test; returns the library status (4 = timeout, the expected outcome)."""
+    return lib().msf_selftest_wait(ctypes.c_uint64(int(limit_ns)), _stream(stream))
