@@ -239,18 +239,35 @@ __device__ __forceinline__ void decode_tile(const TileGeom& tg, int tile, int& i
     b0 = (r % tg.tiles_b) * TILE_B;
 }
 
+// Stage counts of the A-operand ring (one slot = all boxes of one tile), as
+// measured fastest on GB300 for 384 x 384 slices: deeper rings or per-box slots
+// were slower for every variant.
+constexpr int NS_3X3 = 2, NS_LAST = 2, NS_1X1 = 4;
+
 template <int TAPS, int N, int NS, int EPI>
 struct ConvCfg {
-    static constexpr int A_BYTES = TAPS == 9 ? 3 * HALO_BYTES : TILE_BYTES;
+    // A operand ring: NS slots of GROUP TMA boxes each.  A 3x3 tile takes
+    // three boxes (the 18-row halo shifted by dx = -1, 0, +1), a 1x1 tile one
+    // 16-row box; a slot holds a whole tile.
+    static constexpr int BOXES = TAPS == 9 ? 3 : 1;
+    static constexpr int GROUP = BOXES;
+    static constexpr int SLOTS_PER_TILE = BOXES / GROUP;
+    static constexpr int BOX_BYTES = TAPS == 9 ? HALO_BYTES : TILE_BYTES;
+    static constexpr int SLOT_BYTES = GROUP * BOX_BYTES;
     static constexpr int W_BYTES = TAPS * N * 128;
-    static constexpr int O_BYTES = epi_stores_bf16(EPI) ? 2 * TILE_BYTES : 0;
-    static constexpr int BAR_BYTES = 512;   // barriers, TMEM slot, abort flag, bias
-    static constexpr int SMEM = 1024 + NS * A_BYTES + W_BYTES + O_BYTES + BAR_BYTES;
+    static constexpr int O_BYTES = epi_stores_bf16(EPI) ? TILE_BYTES : 0;
+    static constexpr int BAR_BYTES = 512;   // barriers, TMEM slot, abort flag (256 B), bias (256 B)
+    static constexpr int SMEM = 1024 + NS * SLOT_BYTES + W_BYTES + O_BYTES + BAR_BYTES;
+    static_assert(BOXES % GROUP == 0, "a slot group must divide the boxes of a tile");
+    static_assert((2 * NS + 5) * 8 + 8 <= 256, "barrier block overflows into the bias");
+    static_assert(SMEM <= 232448, "more dynamic shared memory than a CTA may have");
 };
 
 // Persistent warp-specialised implicit-GEMM 3x3 (TAPS = 9) or 1x1 (TAPS = 1)
 // convolution over BF16 NHWC activations.  Tile t of the static round-robin
 // sequence blockIdx.x, blockIdx.x + gridDim.x, ... is a 16 x 8 pixel block.
+// The producer streams A boxes through an NS-slot ring; the MMA issuer frees a
+// slot once the taps that read it are issued.
 template <int TAPS, int N, int NS, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
@@ -260,7 +277,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
-    uint8_t* sW = sA + NS * C::A_BYTES;
+    uint8_t* sW = sA + NS * C::SLOT_BYTES;
     uint8_t* sO = sW + C::W_BYTES;
     uint64_t* bars = (uint64_t*)(sO + C::O_BYTES);
     uint64_t* full = bars;
@@ -308,26 +325,30 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             for (int s = 0; s < NS; ++s) issued[s] = 0;
             tc::mbar_expect_tx(wbar, C::W_BYTES);
             for (int tap = 0; tap < TAPS; ++tap) tc::tma_load_2d(sW + tap * N * 128, &map_w, wbar, 0, tap * N);
-            int it = 0;
+            int j = 0;   // box sequence number
             bool ok = true;
-            for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
-                const int s = it % NS, u = it / NS;
-                if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, abort_flag)) {
-                    ok = false;
-                    break;
-                }
+            for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x) {
                 int img, a0, b0;
                 decode_tile(tg, tile, img, a0, b0);
-                uint8_t* dst = sA + s * C::A_BYTES;
-                tc::mbar_expect_tx(&full[s], C::A_BYTES);
-                if (TAPS == 9) {
 #pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
-                        tc::tma_load_4d(dst + dx * HALO_BYTES, &map_a, &full[s], 0, b0 + dx - 1, a0 - 1, img);
-                } else {
-                    tc::tma_load_4d(dst, &map_a, &full[s], 0, b0, a0, img);
+                for (int g = 0; g < C::SLOTS_PER_TILE; ++g, ++j) {
+                    const int s = j % NS, u = j / NS;
+                    if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* dst = sA + s * C::SLOT_BYTES;
+                    tc::mbar_expect_tx(&full[s], C::SLOT_BYTES);
+#pragma unroll
+                    for (int k = 0; k < C::GROUP; ++k) {
+                        const int bx = g * C::GROUP + k;
+                        if (TAPS == 9)
+                            tc::tma_load_4d(dst + k * C::BOX_BYTES, &map_a, &full[s], 0, b0 + bx - 1, a0 - 1, img);
+                        else
+                            tc::tma_load_4d(dst, &map_a, &full[s], 0, b0, a0, img);
+                    }
+                    issued[s] = u + 1;
                 }
-                issued[s] = u + 1;
             }
             if (!ok) {
                 give_up(MSF_ERR_TIMEOUT);
@@ -342,26 +363,38 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             constexpr uint32_t idesc = tc::idesc_bf16<128, N>();
             bool ok = tc::mbar_wait(wbar, 0, abort_flag);
             tc::fence_after_sync();
-            int it = 0;
+            const uint32_t w_base = tc::smem_u32(sW);
+            int it = 0, j = 0;
             for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x, ++it) {
-                const int s = it % NS, u = it / NS, ab = it & 1, ua = it >> 1;
-                if (!tc::mbar_wait(&full[s], u & 1, abort_flag)) { ok = false; break; }
+                const int ab = it & 1, ua = it >> 1;
                 if (ua > 0 && !tc::mbar_wait(&tempty[ab], (ua - 1) & 1, abort_flag)) { ok = false; break; }
                 tc::fence_after_sync();
                 const uint32_t d_tmem = tmem_base + ab * N;
-                const uint32_t a_base = tc::smem_u32(sA + s * C::A_BYTES);
-                const uint32_t w_base = tc::smem_u32(sW);
+                // box bx holds the halo shifted by dx = bx - 1; its three dy
+                // taps start 0, 1 and 2 image rows (1024 B each) into it
 #pragma unroll
-                for (int tap = 0; tap < TAPS; ++tap) {
-                    const uint32_t a_off = TAPS == 9 ? (tap % 3) * HALO_BYTES + (tap / 3) * 1024 : 0;
+                for (int g = 0; g < C::SLOTS_PER_TILE; ++g, ++j) {
+                    const int s = j % NS, u = j / NS;
+                    if (!tc::mbar_wait(&full[s], u & 1, abort_flag)) { ok = false; break; }
+                    tc::fence_after_sync();
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = tc::desc_sw128(a_base + a_off + kk * 32);
-                        const uint64_t bd = tc::desc_sw128(w_base + tap * N * 128 + kk * 32);
-                        tc::mma_bf16(d_tmem, ad, bd, idesc, (tap | kk) ? 1u : 0u);
+                    for (int k = 0; k < C::GROUP; ++k) {
+                        const int bx = g * C::GROUP + k;
+                        const uint32_t a_base = tc::smem_u32(sA + s * C::SLOT_BYTES + k * C::BOX_BYTES);
+#pragma unroll
+                        for (int dy = 0; dy < (TAPS == 9 ? 3 : 1); ++dy) {
+                            const int tap = TAPS == 9 ? dy * 3 + bx : 0;
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = tc::desc_sw128(a_base + dy * 1024 + kk * 32);
+                                const uint64_t bd = tc::desc_sw128(w_base + tap * N * 128 + kk * 32);
+                                tc::mma_bf16(d_tmem, ad, bd, idesc, (bx | dy | kk) ? 1u : 0u);
+                            }
+                        }
                     }
+                    tc::mma_commit(&empty[s]);
                 }
-                tc::mma_commit(&empty[s]);
+                if (!ok) break;
                 tc::mma_commit(&tfull[ab]);
             }
             if (!ok) give_up(MSF_ERR_TIMEOUT);
@@ -402,9 +435,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                 }
                 // per-warp staging: this warp's 32 rows are 4 image rows of
                 // the tile; lane 0 stores them with its own bulk group, so no
-                // barrier spans more than one warp
-                uint8_t* stage = sO + ((it & 1) * 4 + q) * (TILE_BYTES / 4);
-                if (lane == 0) tc::tma_store_wait_read<1>();
+                // barrier spans more than one warp.  The previous tile's store
+                // from this stage must have left shared memory first.
+                uint8_t* stage = sO + q * (TILE_BYTES / 4);
+                if (lane == 0) tc::tma_store_wait_read<0>();
                 __syncwarp();
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
@@ -449,6 +483,252 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- row-pair 3x3 conv
+
+// A 3x3 64 -> 64 layer whose tile puts 16 row PAIRS x 8 columns (256 output
+// pixels) on the 128 accumulator rows: row m = 8 i + j holds pixel
+// (a0 + 2i, b0 + j) in accumulator columns 0-63 (group 0) and pixel
+// (a0 + 2i + 1, b0 + j) in columns 64-127 (group 1).  Input row a0 + 2i + s,
+// s = -1 .. 2, reaches group 0 through kernel row dy = s and group 1 through
+// dy = s - 1, so one A slice feeds both groups with B = [W(dy = s); W(dy = s-1)]
+// (N = 128; N = 64 at s = -1 and s = 2 where one group has no tap).  A
+// tcgen05.mma costs about as much at N = 64 as at N = 128 on this part, so the
+// 12 A slices x 4 K-steps per 256 pixels replace 18 x 4 of the 16 x 8 tile.
+// Rows of one parity come from one TMA box: the activation maps view the
+// image rows as (H / 2 pairs) x (2 parities), which needs an even H.
+constexpr int PAIR_ROWS = 16;                                 // row pairs per tile
+constexpr int PBOX_BYTES = (PAIR_ROWS + 1) * TILE_B * 128;    // 17408: 17 pair rows of one parity
+
+struct PairCfg {
+    static constexpr int NS = 2;                              // stages; one stage = one parity x 3 dx boxes
+    static constexpr int STAGE_BYTES = 3 * PBOX_BYTES;
+    static constexpr int W_BYTES = 9 * CH * 128;
+    static constexpr int O_BYTES = 2 * TILE_BYTES;            // group 0 and group 1 staging
+    static constexpr int BAR_BYTES = 512;
+    static constexpr int SMEM = 1024 + NS * STAGE_BYTES + W_BYTES + O_BYTES + BAR_BYTES;
+    static_assert((2 * NS + 5) * 8 + 8 <= 256, "barrier block overflows into the bias");
+    static_assert(SMEM <= 232448, "more dynamic shared memory than a CTA may have");
+};
+
+__device__ __forceinline__ void decode_pair_tile(const TileGeom& tg, int tile, int& img, int& a0, int& b0) {
+    const int per = tg.tiles_a * tg.tiles_b;
+    img = tile / per;
+    const int r = tile - img * per;
+    a0 = (r / tg.tiles_b) * (2 * PAIR_ROWS);
+    b0 = (r % tg.tiles_b) * TILE_B;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(THREADS, 1)
+conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
+                 const __grid_constant__ CUtensorMap map_out, const float* __restrict__ bias, TileGeom tg,
+                 int* __restrict__ err) {
+    static_assert(EPI == EPI_RELU || EPI == EPI_RAW, "row-pair conv stores BF16 activations");
+    using C = PairCfg;
+    constexpr int NS = C::NS;
+    constexpr uint32_t WBLK = CH * 128;   // one tap's 64 x 64 BF16 weights
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sW = sA + NS * C::STAGE_BYTES;
+    uint8_t* sO = sW + C::W_BYTES;
+    uint64_t* bars = (uint64_t*)(sO + C::O_BYTES);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NS;
+    uint64_t* tfull = bars + 2 * NS;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(wbar + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    float* sbias = (float*)((uint8_t*)bars + 256);
+    if (threadIdx.x < CH) sbias[threadIdx.x] = bias[threadIdx.x];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], 128);
+        }
+        tc::mbar_init(wbar, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, 2 * TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto give_up = [&](int code) {
+        *abort_flag = 1;
+        atomicExch(err, code);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: weights once, then two parity stages per tile
+            int issued[NS];
+            for (int s = 0; s < NS; ++s) issued[s] = 0;
+            // per dx, the blocks W(dy = +1), W(0), W(-1) back to back, so that
+            // [W(s); W(s - 1)] is one contiguous 128-row B operand
+            tc::mbar_expect_tx(wbar, C::W_BYTES);
+            for (int dx = 0; dx < 3; ++dx)
+                for (int d = 0; d < 3; ++d)
+                    tc::tma_load_2d(sW + (dx * 3 + d) * WBLK, &map_w, wbar, 0, ((2 - d) * 3 + dx) * CH);
+            int j = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x) {
+                int img, a0, b0;
+                decode_pair_tile(tg, tile, img, a0, b0);
+#pragma unroll
+                for (int p = 0; p < 2; ++p, ++j) {
+                    const int s = j % NS, u = j / NS;
+                    if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* dst = sA + s * C::STAGE_BYTES;
+                    tc::mbar_expect_tx(&full[s], C::STAGE_BYTES);
+                    // parity p: box entry k is image row a0 - p + 2k (zero-filled outside the image)
+#pragma unroll
+                    for (int bx = 0; bx < 3; ++bx)
+                        tc::tma_load_5d(dst + bx * PBOX_BYTES, &map_a, &full[s], 0, b0 + bx - 1, p, a0 / 2 - p, img);
+                    issued[s] = u + 1;
+                }
+            }
+            if (!ok) {
+                give_up(MSF_ERR_TIMEOUT);
+                for (int s = 0; s < NS; ++s)
+                    if (issued[s] > 0) tc::mbar_wait(&full[s], (issued[s] - 1) & 1, nullptr, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            constexpr uint32_t id128 = tc::idesc_bf16<128, 128>();
+            constexpr uint32_t id64 = tc::idesc_bf16<128, 64>();
+            bool ok = tc::mbar_wait(wbar, 0, abort_flag);
+            tc::fence_after_sync();
+            const uint32_t w_base = tc::smem_u32(sW);
+            int it = 0, j = 0;
+            for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x, ++it) {
+                const int ab = it & 1, ua = it >> 1;
+                if (ua > 0 && !tc::mbar_wait(&tempty[ab], (ua - 1) & 1, abort_flag)) { ok = false; break; }
+                tc::fence_after_sync();
+                const uint32_t d = tmem_base + ab * 2 * CH;
+#pragma unroll
+                for (int p = 0; p < 2; ++p, ++j) {
+                    const int s = j % NS, u = j / NS;
+                    if (!tc::mbar_wait(&full[s], u & 1, abort_flag)) { ok = false; break; }
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int bx = 0; bx < 3; ++bx) {
+                        const uint32_t a = tc::smem_u32(sA + s * C::STAGE_BYTES + bx * PBOX_BYTES);
+                        const uint32_t wb = w_base + bx * 3 * WBLK;   // W(+1, dx) of this dx
+                        if (p == 0) {
+                            // s = 0: group 0 by dy 0, group 1 by dy -1; the first
+                            // of these MMAs initialises all 128 columns
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                tc::mma_bf16(d, tc::desc_sw128(a + kk * 32), tc::desc_sw128(wb + WBLK + kk * 32), id128,
+                                             (bx | kk) ? 1u : 0u);
+                            // s = 2: group 1 by dy +1
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                tc::mma_bf16(d + CH, tc::desc_sw128(a + 1024 + kk * 32), tc::desc_sw128(wb + kk * 32),
+                                             id64, 1u);
+                        } else {
+                            // s = -1: group 0 by dy -1
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                tc::mma_bf16(d, tc::desc_sw128(a + kk * 32), tc::desc_sw128(wb + 2 * WBLK + kk * 32),
+                                             id64, 1u);
+                            // s = +1: group 0 by dy +1, group 1 by dy 0
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                tc::mma_bf16(d, tc::desc_sw128(a + 1024 + kk * 32), tc::desc_sw128(wb + kk * 32), id128,
+                                             1u);
+                        }
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&tfull[ab]);
+            }
+            if (!ok) give_up(MSF_ERR_TIMEOUT);
+        }
+    } else {
+        // ---------------- epilogue: 4 warps, TMEM lane quarter q = warp % 4
+        // holds row pairs 4q .. 4q + 3 of the tile
+        const int q = warp & 3;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
+            const int ab = it & 1, ua = it >> 1;
+            if (!tc::mbar_wait(&tfull[ab], ua & 1, abort_flag)) {
+                give_up(MSF_ERR_TIMEOUT);
+                break;
+            }
+            tc::fence_after_sync();
+            int img, a0, b0;
+            decode_pair_tile(tg, tile, img, a0, b0);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                uint32_t r[CH];
+                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + ab * 2 * CH + g * CH;
+#pragma unroll
+                for (int c = 0; c < CH / 16; ++c) tc::tmem_ld16(taddr + c * 16, r + c * 16);
+                tc::tmem_ld_wait();
+                if (g == 1) {
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&tempty[ab]);
+                }
+                uint32_t w[CH / 2];
+#pragma unroll
+                for (int k = 0; k < CH / 2; ++k) {
+                    float lo = __uint_as_float(r[2 * k]) + sbias[2 * k];
+                    float hi = __uint_as_float(r[2 * k + 1]) + sbias[2 * k + 1];
+                    if (EPI == EPI_RELU) {
+                        lo = fmaxf(lo, 0.0f);
+                        hi = fmaxf(hi, 0.0f);
+                    }
+                    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+                    w[k] = *reinterpret_cast<uint32_t*>(&h);
+                }
+                // group g of this warp: 4 pair rows x 8 pixels, one bulk store;
+                // the previous tile's store from this buffer must have left it
+                uint8_t* stage = sO + (q * 2 + g) * (TILE_BYTES / 4);
+                if (lane == 0) tc::tma_store_wait_read<1>();
+                __syncwarp();
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    *reinterpret_cast<uint4*>(stage + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+                        make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    const int pr = a0 / 2 + 4 * q;
+                    if (pr < tg.H / 2) tc::tma_store_5d(&map_out, stage, 0, b0, g, pr, img);
+                    tc::tma_store_commit();
+                }
+            }
+        }
+        if (lane == 0) tc::tma_store_wait_all();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem_base, 2 * TMEM_COLS);
     }
 }
 
@@ -501,6 +781,24 @@ static msf_status make_w_map(CUtensorMap* m, void* base, int rows_total, int box
     return MSF_OK;
 }
 
+// 5D view of a BF16 activation tensor [imgs][H][W][64], H even: dims
+// (64, W, parity, H / 2, imgs), so that one box holds rows of one parity.
+static msf_status make_pair_map(CUtensorMap* m, void* base, int imgs, int H, int W, int box_pairs) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    if (H % 2) return fail(MSF_ERR_ARG, "row-pair activation map needs an even height, got %d", H);
+    const cuuint64_t row = (cuuint64_t)W * CH * 2;
+    cuuint64_t dims[5] = {(cuuint64_t)CH, (cuuint64_t)W, 2, (cuuint64_t)(H / 2), (cuuint64_t)imgs};
+    cuuint64_t strides[4] = {(cuuint64_t)CH * 2, row, 2 * row, (cuuint64_t)H * row};
+    cuuint32_t box[5] = {(cuuint32_t)CH, (cuuint32_t)TILE_B, 1, (cuuint32_t)box_pairs, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled (row pairs) failed: %d", (int)r);
+    return MSF_OK;
+}
+
 static int g_num_sms = 0;
 
 template <int TAPS, int N, int NS, int EPI>
@@ -518,12 +816,14 @@ static msf_status ensure_kernel_attrs() {
     int dev = 0;
     MSF_TRY_CUDA(cudaGetDevice(&dev));
     MSF_TRY_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    MSF_TRY_CUDA((set_smem_attr<1, 64, 4, EPI_RELU>()));
-    MSF_TRY_CUDA((set_smem_attr<9, 64, 2, EPI_RELU>()));
-    MSF_TRY_CUDA((set_smem_attr<9, 64, 2, EPI_RAW>()));
-    MSF_TRY_CUDA((set_smem_attr<9, 64, 2, EPI_RAW32>()));
-    MSF_TRY_CUDA((set_smem_attr<9, 16, 2, EPI_RESID>()));
-    MSF_TRY_CUDA((set_smem_attr<9, 16, 2, EPI_F32>()));
+    MSF_TRY_CUDA((set_smem_attr<1, 64, NS_1X1, EPI_RELU>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 64, NS_3X3, EPI_RELU>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 64, NS_3X3, EPI_RAW>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 64, NS_3X3, EPI_RAW32>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 16, NS_LAST, EPI_RESID>()));
+    MSF_TRY_CUDA((set_smem_attr<9, 16, NS_LAST, EPI_F32>()));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      PairCfg::SMEM));
     done = true;
     return MSF_OK;
 }
@@ -542,6 +842,19 @@ static msf_status launch_conv(const CUtensorMap& ma, const CUtensorMap& mw, cons
                                   : (EPI == EPI_RAW ? "conv3x3_dgrad_tc" : (EPI == EPI_RAW32 ? "conv3x3_fp32_tc" : "conv3x3_tc"))),
              st);
     kern<<<grid, THREADS, C::SMEM, st>>>(ma, mw, mo, bias, tg, sg, centre, outv, err);
+    MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
+// Row-pair 3x3 layer over images of even height (tg in row-pair tiles).
+template <int EPI>
+static msf_status launch_pair(const CUtensorMap& ma, const CUtensorMap& mw, const CUtensorMap& mo, const float* bias,
+                              const TileGeom& tg, int* err, cudaStream_t st) {
+    MSF_TRY(ensure_kernel_attrs());
+    const int grid = tg.total < g_num_sms ? tg.total : g_num_sms;
+    if (grid <= 0) return MSF_OK;
+    MSF_PROF("conv3x3_tc", st);
+    conv_pair_kernel<EPI><<<grid, THREADS, PairCfg::SMEM, st>>>(ma, mw, mo, bias, tg, err);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
 }
@@ -707,6 +1020,14 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
     }
     for (int l = 0; l < LAYERS; ++l)
         MSF_TRY(make_w_map(&mw[l], c->d_wpack + c->wpack_off[l], taps_of(l) * rows_of(l), rows_of(l)));
+    // images of even height take the row-pair kernel for the 64 -> 64 layers
+    const bool pairs = sg.H % 2 == 0;
+    CUtensorMap p17[2], p4[2];
+    if (pairs)
+        for (int b = 0; b < 2; ++b) {
+            MSF_TRY(make_pair_map(&p17[b], c->d_act[b], imgs_cap, sg.H, sg.W, PAIR_ROWS + 1));
+            MSF_TRY(make_pair_map(&p4[b], c->d_act[b], imgs_cap, sg.H, sg.W, 4));
+        }
     for (int t0 = 0; t0 < vol->nt; t0 += fchunk) {
         sg.t0 = t0;
         sg.nframes = fchunk < vol->nt - t0 ? fchunk : vol->nt - t0;
@@ -743,15 +1064,21 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
         tg.tiles_b = (sg.W + TILE_B - 1) / TILE_B;
         tg.total = tg.imgs * tg.tiles_a * tg.tiles_b;
         int cur = 0;
-        MSF_TRY((launch_conv<1, 64, 4, EPI_RELU>(m16[0], mw[0], m4[1], c->d_bias, tg, sg, nullptr, nullptr,
+        MSF_TRY((launch_conv<1, 64, NS_1X1, EPI_RELU>(m16[0], mw[0], m4[1], c->d_bias, tg, sg, nullptr, nullptr,
                                                 c->d_err, st)));
         cur = 1;
+        TileGeom tp = tg;
+        tp.tiles_a = (sg.H + 2 * PAIR_ROWS - 1) / (2 * PAIR_ROWS);
+        tp.total = tp.imgs * tp.tiles_a * tp.tiles_b;
         for (int l = 1; l < LAYERS - 1; ++l) {
-            MSF_TRY((launch_conv<9, 64, 2, EPI_RELU>(m18[cur], mw[l], m4[cur ^ 1], c->d_bias + l * CH, tg, sg,
-                                                    nullptr, nullptr, c->d_err, st)));
+            if (pairs)
+                MSF_TRY((launch_pair<EPI_RELU>(p17[cur], mw[l], p4[cur ^ 1], c->d_bias + l * CH, tp, c->d_err, st)));
+            else
+                MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RELU>(m18[cur], mw[l], m4[cur ^ 1], c->d_bias + l * CH, tg,
+                                                              sg, nullptr, nullptr, c->d_err, st)));
             cur ^= 1;
         }
-        MSF_TRY((launch_conv<9, 16, 2, EPI_RESID>(m18[cur], mw[LAYERS - 1], m4[cur ^ 1],
+        MSF_TRY((launch_conv<9, 16, NS_LAST, EPI_RESID>(m18[cur], mw[LAYERS - 1], m4[cur ^ 1],
                                                  c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out, c->d_err, st)));
     }
     return MSF_OK;
@@ -1403,9 +1730,9 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         pack_batch_kernel<<<152 * 8, 256, 0, st>>>(d_noisy, (uint4*)w.act[0], B, H, W);
         MSF_LAUNCH_CHECK();
     }
-    MSF_TRY((launch_conv<1, 64, 4, EPI_RELU>(m16[0], mw[0], m4[1], w.bf, tg, sg, nullptr, nullptr, c->d_err, st)));
+    MSF_TRY((launch_conv<1, 64, NS_1X1, EPI_RELU>(m16[0], mw[0], m4[1], w.bf, tg, sg, nullptr, nullptr, c->d_err, st)));
     for (int l = 1; l <= 8; ++l) {
-        MSF_TRY((launch_conv<9, 64, 2, EPI_RAW32>(m18[l], mw[l], m4[l], w.bf + l * CH, tg, sg, nullptr, w.z[l], c->d_err, st)));
+        MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RAW32>(m18[l], mw[l], m4[l], w.bf + l * CH, tg, sg, nullptr, w.z[l], c->d_err, st)));
         double* sums = w.sums + (size_t)(l - 1) * 4 * CH;
         float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
         MSF_TRY(reduce(RED_MOMENTS, w.z[l], nullptr, nullptr, nullptr, nullptr, sums));
@@ -1417,7 +1744,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
             MSF_LAUNCH_CHECK();
         }
     }
-    MSF_TRY((launch_conv<9, 16, 2, EPI_F32>(m18[9], mw[9], m4[9], w.bf + 9 * CH, tg, sg, nullptr, w.R, c->d_err, st)));
+    MSF_TRY((launch_conv<9, 16, NS_LAST, EPI_F32>(m18[9], mw[9], m4[9], w.bf + 9 * CH, tg, sg, nullptr, w.R, c->d_err, st)));
     {
         MSF_PROF("train_loss", st);
         loss_kernel<<<nred, 256, 0, st>>>(d_noisy, d_clean, w.R, w.dR, B, H, W, w.part);
@@ -1460,7 +1787,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
             wgrad_reduce_kernel<<<144, 256, 0, st>>>(w.wpart, nchunks, 9, 0, c->d_grad + o.w[l]);
             MSF_LAUNCH_CHECK();
         }
-        MSF_TRY((launch_conv<9, 64, 2, EPI_RAW>(g18[cur ^ 1], mb[l - 1], g4[cur], w.zeros, tg, sg, nullptr, nullptr,
+        MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RAW>(g18[cur ^ 1], mb[l - 1], g4[cur], w.zeros, tg, sg, nullptr, nullptr,
                                                c->d_err, st)));
         // g[cur] now holds the gradient w.r.t. act[l]
     }

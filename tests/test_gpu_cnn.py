@@ -50,13 +50,19 @@ def _gpu_net(M, convs, bns, stats, max_pixels):
     return c, oracle.fold_bn(cv, bv, sv)
 
 
+# (nt, nz, ny, nx).  Even slice heights run the 64 -> 64 layers as 32 x 8
+# row-pair tiles, odd ones as 16 x 8 tiles; both shapes are ragged against
+# their tiles, and (4, 19, 34, 26) leaves a row-pair tile with one valid pair.
+SHAPES = [(6, 18, 24, 20), (4, 19, 34, 26)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("orient", ["xy", "yz", "zx"])
-def test_denoise_matches_oracle(M, orient):
+def test_denoise_matches_oracle(M, orient, shape):
     import torch
     convs, bns, stats = _net(51)
-    shape = (6, 18, 24, 20)                      # nt, nz, ny, nx: ragged against 16 x 8 tiles
     v = f32(synth.uniform(52, shape, 0.0, 1.5))
-    c, layers = _gpu_net(M, convs, bns, stats, 2 * 24 * 20 * 18)
+    c, layers = _gpu_net(M, convs, bns, stats, 2 * shape[1] * shape[2] * shape[3])
     vol = M.msf_vol(shape[3], shape[2], shape[1], shape[0], 1.0)
     out = torch.empty(shape, device="cuda")
     M.msf_denoise(c, ORIENT[orient], vol, _t(v), out)
