@@ -184,14 +184,19 @@ def algorithmic(scan, K1):
         "conv3x3_tc": ("tensor", 2.0 * 576 * 64 * scan.n ** 3),
         "conv1_tc": ("tensor", 2.0 * 64 * 64 * scan.n ** 3),
         "conv10_tc": ("tensor", 2.0 * 576 * 16 * scan.n ** 3),
+        # last 64 -> 64 layer fused with the output layer's 64 x 9 per-tap products
+        "conv3x3_out_tc": ("tensor", 2.0 * (576 * 64 + 64 * 9) * scan.n ** 3),
+        # output layer's 3 x 3 sum of the nine per-tap planes, centre in, volume out
+        "resid_stencil": ("hbm", (4.0 * 9 + 8.0) * scan.n ** 3),
         "pack5": ("hbm", (4.0 * 5 + 128.0) * scan.n ** 3),
     }
 
 
 # DRAM bytes per pixel of one launch, from the ncu captures summarised under
-# profiles/ (conv3x3_tc: 268.59 MB read + 222.70 MB written over 2 097 152 px of
-# one 128^3 time-point); the traffic of these kernels scales with the pixel count.
-MEASURED_TRAFFIC_PER_PX = {"conv3x3_tc": (268.588288e6 + 222.698496e6) / 2097152}
+# profiles/ of the kernel as it stands (none is listed while a kernel has
+# changed since its capture); the traffic of these kernels scales with the
+# pixel count.
+MEASURED_TRAFFIC_PER_PX = {}
 
 
 def roofline(prof, scan, K1, peaks, steps):

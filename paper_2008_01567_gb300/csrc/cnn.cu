@@ -48,9 +48,11 @@ constexpr int TMEM_COLS = 128;
 // EPI_RAW:   acc + bias -> BF16 (TMA store): pre-BatchNorm outputs and input gradients
 // EPI_RESID: last layer, centre - (acc + bias) -> FP32 4D output volume
 // EPI_F32:   last layer, acc + bias -> FP32 [img][H][W] (training)
+// EPI_PART:  last 64 -> 64 layer fused with the output layer (row-pair kernel):
+//            per-tap output-layer sums -> FP32 planes [9][img][H][W]
 // EPI_RAW32: acc + bias -> FP32 [img][H][W][64] (training: pre-BatchNorm outputs,
 //            kept in FP32 because normalising subtracts their batch mean)
-enum Epi { EPI_RELU = 0, EPI_RESID = 1, EPI_RAW = 2, EPI_F32 = 3, EPI_RAW32 = 4 };
+enum Epi { EPI_RELU = 0, EPI_RESID = 1, EPI_RAW = 2, EPI_F32 = 3, EPI_RAW32 = 4, EPI_PART = 5 };
 
 __host__ __device__ constexpr bool epi_stores_bf16(int e) { return e == EPI_RELU || e == EPI_RAW; }
 
@@ -506,10 +508,11 @@ struct PairCfg {
     static constexpr int NS = 2;                              // stages; one stage = one parity x 3 dx boxes
     static constexpr int STAGE_BYTES = 3 * PBOX_BYTES;
     static constexpr int W_BYTES = 9 * CH * 128;
-    static constexpr int O_BYTES = 2 * TILE_BYTES;            // group 0 and group 1 staging
-    static constexpr int BAR_BYTES = 512;
-    static constexpr int SMEM = 1024 + NS * STAGE_BYTES + W_BYTES + O_BYTES + BAR_BYTES;
-    static_assert((2 * NS + 5) * 8 + 8 <= 256, "barrier block overflows into the bias");
+    static constexpr int W10_BYTES = 16 * 128;                // output layer: 16 rows (9 taps) x 64 channels
+    static constexpr int O_BYTES = 2 * TILE_BYTES;            // staging of group 0 and group 1
+    static constexpr int BAR_BYTES = 512;                     // barriers, TMEM slot, abort flag (256 B), bias (256 B)
+    static constexpr int SMEM = 1024 + NS * STAGE_BYTES + W_BYTES + W10_BYTES + O_BYTES + BAR_BYTES;
+    static_assert((2 * NS + 7) * 8 + 8 <= 256, "barrier block overflows into the bias");
     static_assert(SMEM <= 232448, "more dynamic shared memory than a CTA may have");
 };
 
@@ -521,27 +524,41 @@ __device__ __forceinline__ void decode_pair_tile(const TileGeom& tg, int tile, i
     b0 = (r % tg.tiles_b) * TILE_B;
 }
 
+// EPI_RELU stores relu(acc + bias) as BF16 activations.  EPI_PART is the
+// network's last 64 -> 64 layer fused with the 64 -> 1 output layer: the BF16
+// activations are staged in shared memory only, where eight M128 N16 K16 MMAs
+// per tile multiply them by the output layer's weights arranged as one tap per
+// row (map_w10: [9 taps][64], rows 9-15 zero-filled).  Column t of that product
+// is P_t(p) = sum_c w10[t][c] act(p, c), written to part[t * plane + p];
+// resid_stencil_kernel then forms R(p) = bias + sum_t P_t(p + offset_t).
 template <int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
 conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
-                 const __grid_constant__ CUtensorMap map_out, const float* __restrict__ bias, TileGeom tg,
-                 int* __restrict__ err) {
-    static_assert(EPI == EPI_RELU || EPI == EPI_RAW, "row-pair conv stores BF16 activations");
+                 const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_w10,
+                 const float* __restrict__ bias, TileGeom tg, int* __restrict__ err, float* __restrict__ part,
+                 long long plane) {
+    static_assert(EPI == EPI_RELU || EPI == EPI_PART, "row-pair conv: ReLU layers only");
+    constexpr bool FUSED = EPI == EPI_PART;
     using C = PairCfg;
     constexpr int NS = C::NS;
     constexpr uint32_t WBLK = CH * 128;   // one tap's 64 x 64 BF16 weights
+    constexpr int TMEM_PAIR = FUSED ? 4 * TMEM_COLS : 2 * TMEM_COLS;
+    constexpr uint32_t P_COL = 2 * 2 * CH;   // TMEM columns of the per-tap sums (2 groups x 16)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sW = sA + NS * C::STAGE_BYTES;
-    uint8_t* sO = sW + C::W_BYTES;
+    uint8_t* sW10 = sW + C::W_BYTES;
+    uint8_t* sO = sW10 + C::W10_BYTES;
     uint64_t* bars = (uint64_t*)(sO + C::O_BYTES);
     uint64_t* full = bars;
     uint64_t* empty = bars + NS;
     uint64_t* tfull = bars + 2 * NS;
     uint64_t* tempty = tfull + 2;
     uint64_t* wbar = tempty + 2;
-    uint32_t* tmem_slot = (uint32_t*)(wbar + 1);
+    uint64_t* staged = wbar + 1;     // EPI_PART: activations of a tile staged (128 arrivals)
+    uint64_t* pfull = staged + 1;    // EPI_PART: per-tap sums of a tile in TMEM
+    uint32_t* tmem_slot = (uint32_t*)(pfull + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     float* sbias = (float*)((uint8_t*)bars + 256);
     if (threadIdx.x < CH) sbias[threadIdx.x] = bias[threadIdx.x];
@@ -557,11 +574,13 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             tc::mbar_init(&tempty[b], 128);
         }
         tc::mbar_init(wbar, 1);
+        tc::mbar_init(staged, 128);
+        tc::mbar_init(pfull, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
     }
     if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, 2 * TMEM_COLS);
+        tc::tmem_alloc(tmem_slot, TMEM_PAIR);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -581,10 +600,11 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             for (int s = 0; s < NS; ++s) issued[s] = 0;
             // per dx, the blocks W(dy = +1), W(0), W(-1) back to back, so that
             // [W(s); W(s - 1)] is one contiguous 128-row B operand
-            tc::mbar_expect_tx(wbar, C::W_BYTES);
+            tc::mbar_expect_tx(wbar, C::W_BYTES + (FUSED ? C::W10_BYTES : 0));
             for (int dx = 0; dx < 3; ++dx)
                 for (int d = 0; d < 3; ++d)
                     tc::tma_load_2d(sW + (dx * 3 + d) * WBLK, &map_w, wbar, 0, ((2 - d) * 3 + dx) * CH);
+            if (FUSED) tc::tma_load_2d(sW10, &map_w10, wbar, 0, 0);
             int j = 0;
             bool ok = true;
             for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x) {
@@ -617,9 +637,23 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             // ---------------- MMA issuer
             constexpr uint32_t id128 = tc::idesc_bf16<128, 128>();
             constexpr uint32_t id64 = tc::idesc_bf16<128, 64>();
+            constexpr uint32_t id16 = tc::idesc_bf16<128, 16>();
             bool ok = tc::mbar_wait(wbar, 0, abort_flag);
             tc::fence_after_sync();
             const uint32_t w_base = tc::smem_u32(sW);
+            // EPI_PART: the per-tap sums of tile k, once its activations are staged
+            auto part_mmas = [&](int k) {
+                if (!tc::mbar_wait(staged, k & 1, abort_flag)) return false;
+                tc::fence_after_sync();
+#pragma unroll
+                for (int g = 0; g < 2; ++g)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(tmem_base + P_COL + g * 16, tc::desc_sw128(tc::smem_u32(sO + g * TILE_BYTES) + kk * 32),
+                                     tc::desc_sw128(tc::smem_u32(sW10) + kk * 32), id16, kk ? 1u : 0u);
+                tc::mma_commit(pfull);
+                return true;
+            };
             int it = 0, j = 0;
             for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x, ++it) {
                 const int ab = it & 1, ua = it >> 1;
@@ -664,7 +698,10 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 }
                 if (!ok) break;
                 tc::mma_commit(&tfull[ab]);
+                // the previous tile's per-tap sums queue behind this tile's MMAs
+                if (FUSED && it > 0 && !part_mmas(it - 1)) { ok = false; break; }
             }
+            if (FUSED && ok && it > 0 && !part_mmas(it - 1)) ok = false;
             if (!ok) give_up(MSF_ERR_TIMEOUT);
         }
     } else {
@@ -694,41 +731,102 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 }
                 uint32_t w[CH / 2];
 #pragma unroll
-                for (int k = 0; k < CH / 2; ++k) {
-                    float lo = __uint_as_float(r[2 * k]) + sbias[2 * k];
-                    float hi = __uint_as_float(r[2 * k + 1]) + sbias[2 * k + 1];
-                    if (EPI == EPI_RELU) {
-                        lo = fmaxf(lo, 0.0f);
-                        hi = fmaxf(hi, 0.0f);
-                    }
-                    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-                    w[k] = *reinterpret_cast<uint32_t*>(&h);
+                for (int k = 0; k < CH / 4; ++k) {
+                    const float4 bv = reinterpret_cast<const float4*>(sbias)[k];
+                    const float v0 = fmaxf(__uint_as_float(r[4 * k]) + bv.x, 0.0f);
+                    const float v1 = fmaxf(__uint_as_float(r[4 * k + 1]) + bv.y, 0.0f);
+                    const float v2 = fmaxf(__uint_as_float(r[4 * k + 2]) + bv.z, 0.0f);
+                    const float v3 = fmaxf(__uint_as_float(r[4 * k + 3]) + bv.w, 0.0f);
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(v0, v1), h1 = __floats2bfloat162_rn(v2, v3);
+                    w[2 * k] = *reinterpret_cast<uint32_t*>(&h0);
+                    w[2 * k + 1] = *reinterpret_cast<uint32_t*>(&h1);
                 }
-                // group g of this warp: 4 pair rows x 8 pixels, one bulk store;
-                // the previous tile's store from this buffer must have left it
-                uint8_t* stage = sO + (q * 2 + g) * (TILE_BYTES / 4);
-                if (lane == 0) tc::tma_store_wait_read<1>();
-                __syncwarp();
+                // group g occupies 128 consecutive 128-byte rows (warp q: rows
+                // 32q .. 32q + 31), in the 128-byte swizzle shared by the TMA
+                // store and the MMA operand descriptor
+                uint8_t* stage = sO + g * TILE_BYTES + q * (TILE_BYTES / 4);
+                if (!FUSED) {
+                    // the previous tile's store from this buffer must have left it
+                    if (lane == 0) tc::tma_store_wait_read<1>();
+                    __syncwarp();
+                }
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
                     *reinterpret_cast<uint4*>(stage + lane * 128 + ((c ^ (lane & 7)) << 4)) =
                         make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
                 tc::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    const int pr = a0 / 2 + 4 * q;
-                    if (pr < tg.H / 2) tc::tma_store_5d(&map_out, stage, 0, b0, g, pr, img);
-                    tc::tma_store_commit();
+                if (!FUSED) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        // group g of this warp: 4 pair rows x 8 pixels, one bulk store
+                        const int pr = a0 / 2 + 4 * q;
+                        if (pr < tg.H / 2) tc::tma_store_5d(&map_out, stage, 0, b0, g, pr, img);
+                        tc::tma_store_commit();
+                    }
+                }
+            }
+            if (FUSED) {
+                // hand the staged activations to the MMA warp, then write the
+                // per-tap sums it returns; the staging is free again once they are
+                tc::fence_before_sync();
+                tc::mbar_arrive(staged);
+                if (!tc::mbar_wait(pfull, it & 1, abort_flag)) {
+                    give_up(MSF_ERR_TIMEOUT);
+                    break;
+                }
+                tc::fence_after_sync();
+                uint32_t pv[2][16];
+#pragma unroll
+                for (int g = 0; g < 2; ++g)
+                    tc::tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + P_COL + g * 16, pv[g]);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const int a = a0 + 2 * (4 * q + (lane >> 3)) + g, b = b0 + (lane & 7);
+                    if (a < tg.H && b < tg.W) {
+                        float* dst = part + ((size_t)img * tg.H + a) * tg.W + b;
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) dst[(size_t)t * plane] = __uint_as_float(pv[g][t]);
+                    }
                 }
             }
         }
-        if (lane == 0) tc::tma_store_wait_all();
+        if (!FUSED && lane == 0) tc::tma_store_wait_all();
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem_base, 2 * TMEM_COLS);
+        tc::tmem_dealloc(tmem_base, TMEM_PAIR);
+    }
+}
+
+// Output layer from the per-tap planes of EPI_PART:
+// R(a, b) = bias + sum_{dy,dx} P_{(dy+1)*3+dx+1}(a + dy, b + dx) over taps inside
+// the image (the layer's zero padding), written as centre - R in volume order.
+__global__ void resid_stencil_kernel(const float* __restrict__ part, long long plane, const float* __restrict__ bias,
+                                     SliceGeom sg, const float* __restrict__ centre, float* __restrict__ outv) {
+    const float b10 = bias[0];
+    const int H = sg.H, W = sg.W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < plane;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(p % W);
+        const long long rr = p / W;
+        const int a = (int)(rr % H), img = (int)(rr / H);
+        float R = 0.0f;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (a + dy < 0 || a + dy >= H) continue;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (b + dx < 0 || b + dx >= W) continue;
+                R += __ldg(part + (size_t)((dy + 1) * 3 + dx + 1) * plane + p + (long long)dy * W + dx);
+            }
+        }
+        R += b10;
+        const int t = sg.t0 + img / sg.S, s = img % sg.S;
+        const size_t idx = vol_index(sg, t, s, a, b);
+        outv[idx] = centre[idx] - R;
     }
 }
 
@@ -799,6 +897,22 @@ static msf_status make_pair_map(CUtensorMap* m, void* base, int imgs, int H, int
     return MSF_OK;
 }
 
+// The output layer's packed weights [9 taps][16 rows][64] viewed as one row per
+// tap (row 0 of each tap), box 64 x 16: rows 9-15 lie outside and read as zero.
+static msf_status make_w10_map(CUtensorMap* m, void* base) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)KPACK, 9};
+    cuuint64_t strides[1] = {(cuuint64_t)16 * KPACK * 2};
+    cuuint32_t box[2] = {(cuuint32_t)KPACK, 16};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled (output-layer taps) failed: %d", (int)r);
+    return MSF_OK;
+}
+
 static int g_num_sms = 0;
 
 template <int TAPS, int N, int NS, int EPI>
@@ -824,6 +938,8 @@ static msf_status ensure_kernel_attrs() {
     MSF_TRY_CUDA((set_smem_attr<9, 16, NS_LAST, EPI_F32>()));
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairCfg::SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_PART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      PairCfg::SMEM));
     done = true;
     return MSF_OK;
 }
@@ -848,13 +964,14 @@ static msf_status launch_conv(const CUtensorMap& ma, const CUtensorMap& mw, cons
 
 // Row-pair 3x3 layer over images of even height (tg in row-pair tiles).
 template <int EPI>
-static msf_status launch_pair(const CUtensorMap& ma, const CUtensorMap& mw, const CUtensorMap& mo, const float* bias,
-                              const TileGeom& tg, int* err, cudaStream_t st) {
+static msf_status launch_pair(const CUtensorMap& ma, const CUtensorMap& mw, const CUtensorMap& mo,
+                              const CUtensorMap& mw10, const float* bias, const TileGeom& tg, int* err, cudaStream_t st,
+                              float* part = nullptr, long long plane = 0) {
     MSF_TRY(ensure_kernel_attrs());
     const int grid = tg.total < g_num_sms ? tg.total : g_num_sms;
     if (grid <= 0) return MSF_OK;
-    MSF_PROF("conv3x3_tc", st);
-    conv_pair_kernel<EPI><<<grid, THREADS, PairCfg::SMEM, st>>>(ma, mw, mo, bias, tg, err);
+    MSF_PROF(EPI == EPI_PART ? "conv3x3_out_tc" : "conv3x3_tc", st);
+    conv_pair_kernel<EPI><<<grid, THREADS, PairCfg::SMEM, st>>>(ma, mw, mo, mw10, bias, tg, err, part, plane);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
 }
@@ -1020,14 +1137,17 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
     }
     for (int l = 0; l < LAYERS; ++l)
         MSF_TRY(make_w_map(&mw[l], c->d_wpack + c->wpack_off[l], taps_of(l) * rows_of(l), rows_of(l)));
-    // images of even height take the row-pair kernel for the 64 -> 64 layers
+    // images of even height take the row-pair kernel for the 64 -> 64 layers,
+    // the last of them fused with the output layer
     const bool pairs = sg.H % 2 == 0;
-    CUtensorMap p17[2], p4[2];
-    if (pairs)
+    CUtensorMap p17[2], p4[2], mw10;
+    if (pairs) {
         for (int b = 0; b < 2; ++b) {
             MSF_TRY(make_pair_map(&p17[b], c->d_act[b], imgs_cap, sg.H, sg.W, PAIR_ROWS + 1));
             MSF_TRY(make_pair_map(&p4[b], c->d_act[b], imgs_cap, sg.H, sg.W, 4));
         }
+        MSF_TRY(make_w10_map(&mw10, c->d_wpack + c->wpack_off[LAYERS - 1]));
+    }
     for (int t0 = 0; t0 < vol->nt; t0 += fchunk) {
         sg.t0 = t0;
         sg.nframes = fchunk < vol->nt - t0 ? fchunk : vol->nt - t0;
@@ -1070,16 +1190,31 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
         TileGeom tp = tg;
         tp.tiles_a = (sg.H + 2 * PAIR_ROWS - 1) / (2 * PAIR_ROWS);
         tp.total = tp.imgs * tp.tiles_a * tp.tiles_b;
+        const long long plane = (long long)tg.imgs * sg.H * sg.W;
         for (int l = 1; l < LAYERS - 1; ++l) {
-            if (pairs)
-                MSF_TRY((launch_pair<EPI_RELU>(p17[cur], mw[l], p4[cur ^ 1], c->d_bias + l * CH, tp, c->d_err, st)));
+            if (pairs && l == LAYERS - 2)
+                // per-tap planes of the output layer instead of activations
+                MSF_TRY((launch_pair<EPI_PART>(p17[cur], mw[l], p4[cur ^ 1], mw10, c->d_bias + l * CH, tp, c->d_err,
+                                               st, reinterpret_cast<float*>(c->d_act[cur ^ 1]), plane)));
+            else if (pairs)
+                MSF_TRY((launch_pair<EPI_RELU>(p17[cur], mw[l], p4[cur ^ 1], p4[cur ^ 1], c->d_bias + l * CH, tp,
+                                               c->d_err, st)));
             else
                 MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RELU>(m18[cur], mw[l], m4[cur ^ 1], c->d_bias + l * CH, tg,
                                                               sg, nullptr, nullptr, c->d_err, st)));
             cur ^= 1;
         }
-        MSF_TRY((launch_conv<9, 16, NS_LAST, EPI_RESID>(m18[cur], mw[LAYERS - 1], m4[cur ^ 1],
-                                                 c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out, c->d_err, st)));
+        if (pairs) {
+            MSF_PROF("resid_stencil", st);
+            const long long blocks = (plane + 255) / 256;
+            resid_stencil_kernel<<<(unsigned)(blocks < 152 * 64 ? blocks : 152 * 64), 256, 0, st>>>(
+                reinterpret_cast<const float*>(c->d_act[cur]), plane, c->d_bias + (LAYERS - 1) * CH, sg, d_in, d_out);
+            MSF_LAUNCH_CHECK();
+        } else {
+            MSF_TRY((launch_conv<9, 16, NS_LAST, EPI_RESID>(m18[cur], mw[LAYERS - 1], m4[cur ^ 1],
+                                                            c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out,
+                                                            c->d_err, st)));
+        }
     }
     return MSF_OK;
 }
