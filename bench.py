@@ -182,13 +182,13 @@ def algorithmic(scan, K1):
         "mace_consensus": ("hbm", 4.0 * 3 * K1 * N),
         # tensor-core convolutions: 2*K*N FLOP per pixel, one time-point per launch
         "conv3x3_tc": ("tensor", 2.0 * 576 * 64 * scan.n ** 3),
-        "conv1_tc": ("tensor", 2.0 * 64 * 64 * scan.n ** 3),
+        # first layer built from the five frames: 5 x 4 B in, 64 BF16 channels out
+        "conv1_tc": ("hbm", (4.0 * 5 + 128.0) * scan.n ** 3),
         "conv10_tc": ("tensor", 2.0 * 576 * 16 * scan.n ** 3),
         # last 64 -> 64 layer fused with the output layer's 64 x 9 per-tap products
         "conv3x3_out_tc": ("tensor", 2.0 * (576 * 64 + 64 * 9) * scan.n ** 3),
         # output layer's 3 x 3 sum of the nine per-tap planes, centre in, volume out
         "resid_stencil": ("hbm", (4.0 * 9 + 8.0) * scan.n ** 3),
-        "pack5": ("hbm", (4.0 * 5 + 128.0) * scan.n ** 3),
     }
 
 

@@ -174,57 +174,12 @@ __global__ void orient_transpose_kernel(const float* __restrict__ in, float* __r
     }
 }
 
-// One thread per pixel of the chunk, reading frames already in [S][H][W]
-// order (frames[c] points at time-point t0+tl+c-2, clamped, for tl = 0), so
-// consecutive threads read and write consecutive pixels of an image row.
+// The time-points a chunk of the first layer reads, each already in the
+// agent's [S][H][W] order; f[k] is time-point first + k.
 struct PackFrames {
     const float* f[20];     // frame pointers for time-points first .. first+count-1
     int first, count;
 };
-
-__global__ void pack5_kernel(PackFrames pf, uint4* __restrict__ out, SliceGeom g) {
-    const size_t per_frame = (size_t)g.S * g.H * g.W;
-    const size_t total = per_frame * g.nframes;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
-        const int tl = (int)(p / per_frame);
-        const size_t r = p % per_frame;               // s*H*W + a*W + b
-        const int b = (int)(r % g.W), a = (int)((r / g.W) % g.H);
-        const int t = g.t0 + tl;
-        const bool interior = a >= 1 && a <= g.H - 2 && b >= 1 && b <= g.W - 2;
-        float v[FRAMES * 9];
-#pragma unroll
-        for (int c = 0; c < FRAMES; ++c) {
-            const int tc = min(max(t + c - 2, 0), g.nt - 1);
-            const float* f = pf.f[tc - pf.first] + r;
-            if (interior) {
-#pragma unroll
-                for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) v[c * 9 + ky * 3 + kx] = __ldg(f + (ky - 1) * g.W + (kx - 1));
-            } else {
-#pragma unroll
-                for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) {
-                        const int aa = a + ky - 1, bb = b + kx - 1;
-                        v[c * 9 + ky * 3 + kx] =
-                            (aa >= 0 && aa < g.H && bb >= 0 && bb < g.W) ? __ldg(f + (ky - 1) * g.W + (kx - 1)) : 0.0f;
-                    }
-            }
-        }
-        uint32_t w[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const float lo = 2 * i < FRAMES * 9 ? v[2 * i] : 0.0f;
-            const float hi = 2 * i + 1 < FRAMES * 9 ? v[2 * i + 1] : 0.0f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-            w[i] = *reinterpret_cast<uint32_t*>(&h);
-        }
-        uint4* dst = out + p * 8;    // [tl*S + s][a][b] is p itself
-#pragma unroll
-        for (int c = 0; c < 8; ++c) dst[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-    }
-}
 
 // ---------------------------------------------------------------- tcgen05 conv
 
@@ -483,6 +438,272 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- fused first layer
+
+// First layer (3x3 over the 5 frames, Eq. (14)'s 2.5D input) as one persistent
+// kernel.  TMA brings each tile's five FP32 frame patches (rows a0 - 1 ..
+// a0 + 4, columns b0 - 4 .. b0 + 35, zero outside the image) into a ring;
+// producer warps build each pixel's 45 inputs (5 frames x 3 x 3, padded to
+// K = 64, k = frame * 9 + ky * 3 + kx) as a 128-byte BF16 row in shared
+// memory; one MMA warp multiplies a 128-pixel tile by the packed 64 x 64
+// weights (four K16 steps); four epilogue warps store relu(acc + bias) as BF16
+// activations.  A tile is 4 image rows x 32 columns; tile row q is accumulator
+// lanes 32q .. 32q + 31.
+constexpr int C1_ROWS = 4, C1_COLS = 32;
+constexpr int C1_THREADS = 288;   // warp 0 MMA, warps 1-4 producers, warps 5-8 epilogue
+
+constexpr int C1_PCOLS = C1_COLS + 8, C1_PROWS = C1_ROWS + 2;   // frame patch: 40 x 6 FP32
+
+struct C1Cfg {
+    static constexpr int NS = 4;                              // A-operand stages
+    static constexpr int NF = 4;                              // frame-patch stages
+    static constexpr int STAGE_BYTES = TILE_BYTES;            // 128 rows x 128 B
+    static constexpr int PATCH_BYTES = C1_PCOLS * C1_PROWS * 4;   // 960 B copied per patch
+    static constexpr int PATCH_STRIDE = 1024;                 // patches 128-byte aligned in shared memory
+    static constexpr int F_BYTES = FRAMES * PATCH_STRIDE;     // one tile's five patches
+    static constexpr int W_BYTES = CH * 128;
+    static constexpr int O_BYTES = TILE_BYTES;
+    static constexpr int BAR_BYTES = 512;
+    static constexpr int SMEM = 1024 + NS * STAGE_BYTES + W_BYTES + O_BYTES + NF * F_BYTES + BAR_BYTES;
+    static_assert((2 * NS + 2 * NF + 5) * 8 + 8 <= 256, "barrier block overflows into the bias");
+    static_assert(F_BYTES % 128 == 0, "frame stages must stay 128-byte aligned");
+};
+
+__device__ __forceinline__ void decode_c1_tile(const TileGeom& tg, int tile, int& img, int& a0, int& b0) {
+    const int per = tg.tiles_a * tg.tiles_b;
+    img = tile / per;
+    const int r = tile - img * per;
+    a0 = (r / tg.tiles_b) * C1_ROWS;
+    b0 = (r % tg.tiles_b) * C1_COLS;
+}
+
+// PATCH = false (image width not a multiple of 4, which the frame tensor map
+// cannot stride) reads the frames with plain loads instead of the patch ring.
+template <bool PATCH>
+__global__ void __launch_bounds__(C1_THREADS, 1)
+conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_out,
+                   const __grid_constant__ CUtensorMap map_f, const float* __restrict__ bias, PackFrames pf,
+                   SliceGeom g, TileGeom tg, int* __restrict__ err) {
+    using C = C1Cfg;
+    constexpr int NS = C::NS, NF = C::NF;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sW = sA + NS * C::STAGE_BYTES;
+    uint8_t* sO = sW + C::W_BYTES;
+    uint8_t* sF = sO + C::O_BYTES;
+    uint64_t* bars = (uint64_t*)(sF + NF * C::F_BYTES);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NS;
+    uint64_t* ffull = bars + 2 * NS;
+    uint64_t* fempty = ffull + NF;   // all 128 producers have read a patch stage
+    uint64_t* tfull = fempty + NF;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(wbar + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    float* sbias = (float*)((uint8_t*)bars + 256);
+    if (threadIdx.x < CH) sbias[threadIdx.x] = bias[threadIdx.x];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&full[s], 128);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int f = 0; f < NF; ++f) {
+            tc::mbar_init(&ffull[f], 1);
+            tc::mbar_init(&fempty[f], 128);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], 128);
+        }
+        tc::mbar_init(wbar, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto give_up = [&](int code) {
+        *abort_flag = 1;
+        atomicExch(err, code);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- weights, then the MMA issuer
+            constexpr uint32_t idesc = tc::idesc_bf16<128, CH>();
+            tc::mbar_expect_tx(wbar, C::W_BYTES);
+            tc::tma_load_2d(sW, &map_w, wbar, 0, 0);
+            bool ok = tc::mbar_wait(wbar, 0, abort_flag);
+            tc::fence_after_sync();
+            const uint32_t w_base = tc::smem_u32(sW);
+            int it = 0;
+            for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x, ++it) {
+                const int s = it % NS, u = it / NS, ab = it & 1, ua = it >> 1;
+                if (ua > 0 && !tc::mbar_wait(&tempty[ab], (ua - 1) & 1, abort_flag)) { ok = false; break; }
+                if (!tc::mbar_wait(&full[s], u & 1, abort_flag)) { ok = false; break; }
+                tc::fence_after_sync();
+                const uint32_t a_base = tc::smem_u32(sA + s * C::STAGE_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_bf16(tmem_base + ab * CH, tc::desc_sw128(a_base + kk * 32), tc::desc_sw128(w_base + kk * 32),
+                                 idesc, kk ? 1u : 0u);
+                tc::mma_commit(&empty[s]);
+                tc::mma_commit(&tfull[ab]);
+            }
+            if (!ok) give_up(MSF_ERR_TIMEOUT);
+        }
+    } else if (warp <= 4) {
+        // ---------------- producers: warp 1 + r builds tile row r; thread 32
+        // (warp 1, lane 0) also issues the frame-patch copies NF tiles ahead
+        const int r = warp - 1;
+        const bool loader = PATCH && threadIdx.x == 32;
+        auto load_patches = [&](int tile, int fs) {
+            int img, a0, b0;
+            decode_c1_tile(tg, tile, img, a0, b0);
+            const int t = g.t0 + img / g.S, sl = img % g.S;
+            tc::mbar_expect_tx(&ffull[fs], FRAMES * C::PATCH_BYTES);
+#pragma unroll
+            for (int c = 0; c < FRAMES; ++c) {
+                const int tc_ = min(max(t + c - 2, 0), g.nt - 1);
+                tc::tma_load_4d(sF + fs * C::F_BYTES + c * C::PATCH_STRIDE, &map_f, &ffull[fs], b0 - 4, a0 - 1, sl,
+                                tc_ - pf.first);
+            }
+        };
+        if (loader)
+            for (int k = 0; k < NF && blockIdx.x + k * gridDim.x < tg.total; ++k)
+                load_patches(blockIdx.x + k * gridDim.x, k);
+        int it = 0;
+        for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
+            const int s = it % NS, u = it / NS, fs = it % NF, fu = it / NF;
+            if ((PATCH && !tc::mbar_wait(&ffull[fs], fu & 1, abort_flag)) ||
+                (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, abort_flag))) {
+                give_up(MSF_ERR_TIMEOUT);
+                break;
+            }
+            float v[FRAMES * 9];
+            if (PATCH) {
+                // pixel (a0 + r, b0 + lane): patch row r + ky, column lane + kx + 3
+                const float* patch = reinterpret_cast<const float*>(sF + fs * C::F_BYTES) + r * C1_PCOLS + lane + 3;
+#pragma unroll
+                for (int k = 0; k < FRAMES * 9; ++k)
+                    v[k] = patch[(k / 9) * (C::PATCH_STRIDE / 4) + ((k % 9) / 3) * C1_PCOLS + (k % 3)];
+            } else {
+                int img, a0, b0;
+                decode_c1_tile(tg, tile, img, a0, b0);
+                const int a = a0 + r, b = b0 + lane;
+#pragma unroll
+                for (int k = 0; k < FRAMES * 9; ++k) v[k] = 0.0f;
+                if (a < g.H && b < g.W) {
+                    const int t = g.t0 + img / g.S, sl = img % g.S;
+                    const size_t off = ((size_t)sl * g.H + a) * g.W + b;
+#pragma unroll
+                    for (int c = 0; c < FRAMES; ++c) {
+                        const int tc_ = min(max(t + c - 2, 0), g.nt - 1);
+                        const float* f = pf.f[tc_ - pf.first] + off;
+#pragma unroll
+                        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                            for (int kx = 0; kx < 3; ++kx)
+                                if (a + ky - 1 >= 0 && a + ky - 1 < g.H && b + kx - 1 >= 0 && b + kx - 1 < g.W)
+                                    v[c * 9 + ky * 3 + kx] = __ldg(f + (ky - 1) * g.W + (kx - 1));
+                    }
+                }
+            }
+            uint32_t w[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float lo = 2 * i < FRAMES * 9 ? v[2 * i] : 0.0f;
+                const float hi = 2 * i + 1 < FRAMES * 9 ? v[2 * i + 1] : 0.0f;
+                __nv_bfloat162 hv = __floats2bfloat162_rn(lo, hi);
+                w[i] = *reinterpret_cast<uint32_t*>(&hv);
+            }
+            const int m = r * 32 + lane;     // accumulator row of this pixel
+            uint8_t* row = sA + s * C::STAGE_BYTES + m * 128;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<uint4*>(row + ((c ^ (m & 7)) << 4)) =
+                    make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&full[s]);
+            if (PATCH) {
+                // once every producer is done with patch stage fs, refill it NF tiles ahead
+                tc::mbar_arrive(&fempty[fs]);
+                if (loader && tile + NF * (int)gridDim.x < tg.total) {
+                    if (!tc::mbar_wait(&fempty[fs], fu & 1, abort_flag)) {
+                        give_up(MSF_ERR_TIMEOUT);
+                        break;
+                    }
+                    tc::fence_proxy_async_smem();
+                    load_patches(tile + NF * gridDim.x, fs);
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warp 5 + i, TMEM lane quarter q = warp % 4 = tile row q
+        const int q = warp & 3;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
+            const int ab = it & 1, ua = it >> 1;
+            if (!tc::mbar_wait(&tfull[ab], ua & 1, abort_flag)) {
+                give_up(MSF_ERR_TIMEOUT);
+                break;
+            }
+            tc::fence_after_sync();
+            uint32_t r[CH];
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + ab * CH;
+#pragma unroll
+            for (int c = 0; c < CH / 16; ++c) tc::tmem_ld16(taddr + c * 16, r + c * 16);
+            tc::tmem_ld_wait();
+            tc::fence_before_sync();
+            tc::mbar_arrive(&tempty[ab]);
+            int img, a0, b0;
+            decode_c1_tile(tg, tile, img, a0, b0);
+            uint32_t w[CH / 2];
+#pragma unroll
+            for (int k = 0; k < CH / 4; ++k) {
+                const float4 bv = reinterpret_cast<const float4*>(sbias)[k];
+                const float v0 = fmaxf(__uint_as_float(r[4 * k]) + bv.x, 0.0f);
+                const float v1 = fmaxf(__uint_as_float(r[4 * k + 1]) + bv.y, 0.0f);
+                const float v2 = fmaxf(__uint_as_float(r[4 * k + 2]) + bv.z, 0.0f);
+                const float v3 = fmaxf(__uint_as_float(r[4 * k + 3]) + bv.w, 0.0f);
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(v0, v1), h1 = __floats2bfloat162_rn(v2, v3);
+                w[2 * k] = *reinterpret_cast<uint32_t*>(&h0);
+                w[2 * k + 1] = *reinterpret_cast<uint32_t*>(&h1);
+            }
+            uint8_t* stage = sO + q * (TILE_BYTES / 4);
+            if (lane == 0) tc::tma_store_wait_read<0>();
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<uint4*>(stage + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+                    make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                if (a0 + q < tg.H) tc::tma_store_4d(&map_out, stage, 0, b0, a0 + q, img);
+                tc::tma_store_commit();
+            }
+        }
+        if (lane == 0) tc::tma_store_wait_all();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem_base, TMEM_COLS);
     }
@@ -804,30 +1025,69 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
 // Output layer from the per-tap planes of EPI_PART:
 // R(a, b) = bias + sum_{dy,dx} P_{(dy+1)*3+dx+1}(a + dy, b + dx) over taps inside
 // the image (the layer's zero padding), written as centre - R in volume order.
-__global__ void resid_stencil_kernel(const float* __restrict__ part, long long plane, const float* __restrict__ bias,
-                                     SliceGeom sg, const float* __restrict__ centre, float* __restrict__ outv) {
+// A block covers 32 (u) x 32 (b) outputs of one frame: u is the image row a
+// (xy-t, zx-t) or the slice s (yz-t), and `w` the remaining index.  The planes
+// are read along b; the volume is contiguous along b for xy-t, along s for
+// yz-t and along a for zx-t, so the last two write through a shared-memory
+// transpose.
+template <int ORIENT>
+__global__ void __launch_bounds__(256) resid_stencil_kernel(const float* __restrict__ part, long long plane,
+                                                            const float* __restrict__ bias, SliceGeom sg,
+                                                            const float* __restrict__ centre, float* __restrict__ outv) {
+    __shared__ float tile[32][33];
+    const int H = sg.H, W = sg.W, S = sg.S;
+    const int U = ORIENT == 1 ? S : H, NW = ORIENT == 1 ? H : S;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int b0 = blockIdx.x * 32, u0 = blockIdx.y * 32;
     const float b10 = bias[0];
-    const int H = sg.H, W = sg.W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < plane;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(p % W);
-        const long long rr = p / W;
-        const int a = (int)(rr % H), img = (int)(rr / H);
-        float R = 0.0f;
+    for (int z = blockIdx.z; z < sg.nframes * NW; z += gridDim.z) {
+        const int f = z / NW, w = z % NW;
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            if (a + dy < 0 || a + dy >= H) continue;
+        for (int k = 0; k < 4; ++k) {
+            const int u = u0 + ty + 8 * k, b = b0 + tx;
+            if (u >= U || b >= W) continue;
+            const int a = ORIENT == 1 ? w : u, s = ORIENT == 1 ? u : w;
+            const long long p = ((long long)(f * S + s) * H + a) * W + b;
+            float R = 0.0f;
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (b + dx < 0 || b + dx >= W) continue;
-                R += __ldg(part + (size_t)((dy + 1) * 3 + dx + 1) * plane + p + (long long)dy * W + dx);
+            for (int dy = -1; dy <= 1; ++dy) {
+                if (a + dy < 0 || a + dy >= H) continue;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (b + dx < 0 || b + dx >= W) continue;
+                    R += __ldg(part + (size_t)((dy + 1) * 3 + dx + 1) * plane + p + (long long)dy * W + dx);
+                }
+            }
+            R += b10;
+            if (ORIENT == 0) {
+                const size_t idx = vol_index(sg, sg.t0 + f, s, a, b);
+                outv[idx] = centre[idx] - R;
+            } else {
+                tile[ty + 8 * k][tx] = R;
             }
         }
-        R += b10;
-        const int t = sg.t0 + img / sg.S, s = img % sg.S;
-        const size_t idx = vol_index(sg, t, s, a, b);
-        outv[idx] = centre[idx] - R;
+        if (ORIENT != 0) {
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int u = u0 + tx, b = b0 + ty + 8 * k;
+                if (u >= U || b >= W) continue;
+                const int a = ORIENT == 1 ? w : u, s = ORIENT == 1 ? u : w;
+                const size_t idx = vol_index(sg, sg.t0 + f, s, a, b);
+                outv[idx] = centre[idx] - tile[tx][ty + 8 * k];
+            }
+            __syncthreads();
+        }
     }
+}
+
+template <int ORIENT>
+static void launch_stencil(const float* part, long long plane, const float* bias, const SliceGeom& sg,
+                           const float* centre, float* outv, cudaStream_t st) {
+    const int U = ORIENT == 1 ? sg.S : sg.H, NW = ORIENT == 1 ? sg.H : sg.S;
+    const int nz = sg.nframes * NW;
+    const dim3 grid((unsigned)((sg.W + 31) / 32), (unsigned)((U + 31) / 32), (unsigned)(nz < 65535 ? nz : 65535));
+    resid_stencil_kernel<ORIENT><<<grid, dim3(32, 8), 0, st>>>(part, plane, bias, sg, centre, outv);
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -850,12 +1110,13 @@ static EncodeTiledFn encode_fn() {
 }
 
 // 4D BF16 activation tensor [imgs][H][W][64] with a box of 64 x 8 x rows x 1.
-static msf_status make_act_map(CUtensorMap* m, void* base, int imgs, int H, int W, int box_rows) {
+static msf_status make_act_map(CUtensorMap* m, void* base, int imgs, int H, int W, int box_rows,
+                               int box_cols = TILE_B) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)imgs};
     cuuint64_t strides[3] = {(cuuint64_t)CH * 2, (cuuint64_t)W * CH * 2, (cuuint64_t)H * W * CH * 2};
-    cuuint32_t box[4] = {(cuuint32_t)CH, (cuuint32_t)TILE_B, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[4] = {(cuuint32_t)CH, (cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -913,6 +1174,23 @@ static msf_status make_w10_map(CUtensorMap* m, void* base) {
     return MSF_OK;
 }
 
+// FP32 frames [count][S][H][W], consecutive in memory, with a box of one patch
+// of the first layer (C1_PCOLS x C1_PROWS of one slice of one frame).
+static msf_status make_frame_map(CUtensorMap* m, const float* base, int S, int H, int W, int count) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    if ((W * 4) % 16) return fail(MSF_ERR_ARG, "first-layer frame map needs W a multiple of 4, got %d", W);
+    cuuint64_t dims[4] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)S, (cuuint64_t)count};
+    cuuint64_t strides[3] = {(cuuint64_t)W * 4, (cuuint64_t)H * W * 4, (cuuint64_t)S * H * W * 4};
+    cuuint32_t box[4] = {(cuuint32_t)C1_PCOLS, (cuuint32_t)C1_PROWS, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled (frames) failed: %d", (int)r);
+    return MSF_OK;
+}
+
 static int g_num_sms = 0;
 
 template <int TAPS, int N, int NS, int EPI>
@@ -938,6 +1216,10 @@ static msf_status ensure_kernel_attrs() {
     MSF_TRY_CUDA((set_smem_attr<9, 16, NS_LAST, EPI_F32>()));
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairCfg::SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv1_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      C1Cfg::SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv1_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      C1Cfg::SMEM));
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_PART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairCfg::SMEM));
     done = true;
@@ -1129,12 +1411,13 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
     if (!c->folded) MSF_TRY(fold_all(c, st));
     const int fchunk = (int)(c->max_pixels / per_frame < 16 ? c->max_pixels / per_frame : 16);
     const int imgs_cap = fchunk * sg.S;
-    CUtensorMap m16[2], m18[2], m4[2], mw[LAYERS];
+    CUtensorMap m18[2], m4[2], mw[LAYERS];
     for (int b = 0; b < 2; ++b) {
-        MSF_TRY(make_act_map(&m16[b], c->d_act[b], imgs_cap, sg.H, sg.W, TILE_A));
         MSF_TRY(make_act_map(&m18[b], c->d_act[b], imgs_cap, sg.H, sg.W, TILE_A + 2));
         MSF_TRY(make_act_map(&m4[b], c->d_act[b], imgs_cap, sg.H, sg.W, TILE_A / 4));
     }
+    CUtensorMap m1o;   // first-layer output: one row of 32 pixels per store
+    MSF_TRY(make_act_map(&m1o, c->d_act[1], imgs_cap, sg.H, sg.W, 1, C1_COLS));
     for (int l = 0; l < LAYERS; ++l)
         MSF_TRY(make_w_map(&mw[l], c->d_wpack + c->wpack_off[l], taps_of(l) * rows_of(l), rows_of(l)));
     // images of even height take the row-pair kernel for the 64 -> 64 layers,
@@ -1174,8 +1457,26 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
                     pf.f[k] = dst;
                 }
             }
-            MSF_PROF("pack5", st);
-            pack5_kernel<<<152 * 16, 256, 0, st>>>(pf, reinterpret_cast<uint4*>(c->d_act[0]), sg);
+            // first layer straight from the frames
+            TileGeom t1;
+            t1.H = sg.H; t1.W = sg.W; t1.imgs = sg.nframes * sg.S;
+            t1.tiles_a = (sg.H + C1_ROWS - 1) / C1_ROWS;
+            t1.tiles_b = (sg.W + C1_COLS - 1) / C1_COLS;
+            t1.total = t1.imgs * t1.tiles_a * t1.tiles_b;
+            MSF_TRY(ensure_kernel_attrs());
+            MSF_PROF("conv1_tc", st);
+            // the patch ring needs the frames consecutive (they are: the input
+            // volume or the transposed copies) and rows of a multiple of 16 bytes
+            const int grid1 = t1.total < g_num_sms ? t1.total : g_num_sms;
+            if (sg.W % 4 == 0) {
+                CUtensorMap mf;
+                MSF_TRY(make_frame_map(&mf, pf.f[0], sg.S, sg.H, sg.W, pf.count));
+                conv1_fused_kernel<true><<<grid1, C1_THREADS, C1Cfg::SMEM, st>>>(mw[0], m1o, mf, c->d_bias, pf, sg, t1,
+                                                                                   c->d_err);
+            } else {
+                conv1_fused_kernel<false><<<grid1, C1_THREADS, C1Cfg::SMEM, st>>>(mw[0], m1o, m1o, c->d_bias, pf, sg,
+                                                                                    t1, c->d_err);
+            }
             MSF_LAUNCH_CHECK();
         }
         TileGeom tg;
@@ -1183,10 +1484,7 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
         tg.tiles_a = (sg.H + TILE_A - 1) / TILE_A;
         tg.tiles_b = (sg.W + TILE_B - 1) / TILE_B;
         tg.total = tg.imgs * tg.tiles_a * tg.tiles_b;
-        int cur = 0;
-        MSF_TRY((launch_conv<1, 64, NS_1X1, EPI_RELU>(m16[0], mw[0], m4[1], c->d_bias, tg, sg, nullptr, nullptr,
-                                                c->d_err, st)));
-        cur = 1;
+        int cur = 1;
         TileGeom tp = tg;
         tp.tiles_a = (sg.H + 2 * PAIR_ROWS - 1) / (2 * PAIR_ROWS);
         tp.total = tp.imgs * tp.tiles_a * tp.tiles_b;
@@ -1206,9 +1504,11 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
         }
         if (pairs) {
             MSF_PROF("resid_stencil", st);
-            const long long blocks = (plane + 255) / 256;
-            resid_stencil_kernel<<<(unsigned)(blocks < 152 * 64 ? blocks : 152 * 64), 256, 0, st>>>(
-                reinterpret_cast<const float*>(c->d_act[cur]), plane, c->d_bias + (LAYERS - 1) * CH, sg, d_in, d_out);
+            const float* part = reinterpret_cast<const float*>(c->d_act[cur]);
+            const float* b10 = c->d_bias + (LAYERS - 1) * CH;
+            if (orient == MSF_XY_T) launch_stencil<0>(part, plane, b10, sg, d_in, d_out, st);
+            else if (orient == MSF_YZ_T) launch_stencil<1>(part, plane, b10, sg, d_in, d_out, st);
+            else launch_stencil<2>(part, plane, b10, sg, d_in, d_out, st);
             MSF_LAUNCH_CHECK();
         } else {
             MSF_TRY((launch_conv<9, 16, NS_LAST, EPI_RESID>(m18[cur], mw[LAYERS - 1], m4[cur ^ 1],
