@@ -51,32 +51,77 @@ struct MaceCoef {
 
 // W_i += 2 rho (sum_j mu_j (2 X_j - W_j) - X_i) for every agent i, and the
 // partial sums of sum_i mu_i (X_i - Xbar)^2 and Xbar^2 with Xbar = sum_i mu_i X_i.
-template <int K1>
+// Each thread takes four consecutive voxels per step (float4 traffic; N a
+// multiple of 4 and 16-byte aligned stacks, which the caller checks, else
+// VEC = false); the per-voxel
+// terms are FP32 and each step's sum of four is added to FP64 thread sums,
+// so this HBM-bound pass does a few FP64 adds per four voxels.
+template <int K1, bool VEC>
 __global__ void __launch_bounds__(256) consensus_kernel(float* __restrict__ W, const float* __restrict__ X,
                                                          size_t N, MaceCoef c, double* __restrict__ partial) {
     double num = 0.0, den = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-        float x[K1], w[K1];
-#pragma unroll
-        for (int k = 0; k < K1; ++k) {
-            x[k] = X[(size_t)k * N + i];
-            w[k] = W[(size_t)k * N + i];
-        }
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    auto voxel = [&](const float (&x)[K1], float (&w)[K1], float& dev, float& xb2) {
         float zbar = 0.0f, xbar = 0.0f;
 #pragma unroll
         for (int k = 0; k < K1; ++k) {
             zbar += c.mu[k] * (2.0f * x[k] - w[k]);
             xbar += c.mu[k] * x[k];
         }
-        double dev = 0.0;
+        dev = 0.0f;
 #pragma unroll
         for (int k = 0; k < K1; ++k) {
-            W[(size_t)k * N + i] = w[k] + c.two_rho * (zbar - x[k]);
-            const double dxk = (double)x[k] - (double)xbar;
-            dev += (double)c.mu[k] * dxk * dxk;
+            w[k] = w[k] + c.two_rho * (zbar - x[k]);
+            const float dxk = x[k] - xbar;
+            dev = fmaf(c.mu[k] * dxk, dxk, dev);
         }
-        num += dev;
-        den += (double)xbar * (double)xbar;
+        xb2 = xbar * xbar;
+    };
+    if (VEC) {
+        const size_t N4 = N / 4;
+        const float4* X4 = reinterpret_cast<const float4*>(X);
+        float4* W4 = reinterpret_cast<float4*>(W);
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N4; i += stride) {
+            float4 xv[K1], wv[K1];
+#pragma unroll
+            for (int k = 0; k < K1; ++k) {
+                xv[k] = X4[(size_t)k * N4 + i];
+                wv[k] = W4[(size_t)k * N4 + i];
+            }
+            float dsum = 0.0f, bsum = 0.0f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float x[K1], w[K1], dev, xb2;
+#pragma unroll
+                for (int k = 0; k < K1; ++k) {
+                    x[k] = reinterpret_cast<const float*>(&xv[k])[e];
+                    w[k] = reinterpret_cast<const float*>(&wv[k])[e];
+                }
+                voxel(x, w, dev, xb2);
+#pragma unroll
+                for (int k = 0; k < K1; ++k) reinterpret_cast<float*>(&wv[k])[e] = w[k];
+                dsum += dev;
+                bsum += xb2;
+            }
+#pragma unroll
+            for (int k = 0; k < K1; ++k) W4[(size_t)k * N4 + i] = wv[k];
+            num += (double)dsum;
+            den += (double)bsum;
+        }
+    } else {
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+            float x[K1], w[K1], dev, xb2;
+#pragma unroll
+            for (int k = 0; k < K1; ++k) {
+                x[k] = X[(size_t)k * N + i];
+                w[k] = W[(size_t)k * N + i];
+            }
+            voxel(x, w, dev, xb2);
+#pragma unroll
+            for (int k = 0; k < K1; ++k) W[(size_t)k * N + i] = w[k];
+            num += (double)dev;
+            den += (double)xb2;
+        }
     }
     const double sn = block_sum_f64(num);
     const double sd = block_sum_f64(den);
@@ -139,10 +184,15 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
     c.K1 = K1;
     {
         MSF_PROF("mace_consensus", st);
-        if (K1 == 2)
-            consensus_kernel<2><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
+        const bool vec = N % 4 == 0 && (uintptr_t)d.d_W % 16 == 0 && (uintptr_t)d.d_X % 16 == 0;
+        if (K1 == 2 && vec)
+            consensus_kernel<2, true><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
+        else if (K1 == 2)
+            consensus_kernel<2, false><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
+        else if (vec)
+            consensus_kernel<4, true><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
         else
-            consensus_kernel<4><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
+            consensus_kernel<4, false><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
         MSF_LAUNCH_CHECK();
     }
     {

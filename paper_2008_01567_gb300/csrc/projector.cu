@@ -5,8 +5,8 @@
 // cone-beam reference; the geometry is documented in msf.h).  The adjoint is a
 // voxel-driven gather: each voxel enumerates the rays whose bilinear footprint
 // touches it and recomputes the forward's interpolation coordinates with the
-// same FP32 operations, so A^T is exactly the transpose of the FP32 A up to
-// summation order, without atomics.
+// same FP32 operations (the z crossing to within a few 1e-6 voxel): A^T is the
+// transpose of the FP32 A up to rounding, without atomics.
 //
 // Per (view, detector column) constants are computed once in FP64 and stored
 // in FP32.  A ray's direction has d_x, d_y fixed by its column and d_z = v, so
@@ -147,10 +147,32 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
 
 enum FwdMode { FWD_PLAIN = 0, FWD_LAMBDA = 1, FWD_RESIDUAL = 2 };
 
-// One thread per ray; a block covers blockDim.x columns x blockDim.y rows of one
-// view (128 threads; the shape is chosen per plan by msf_projector_autotune).  x-major rays
-// read the transposed frame [nz][nx][ny], y-major rays the natural frame
-// [nz][ny][nx], so in both cases the minor in-plane axis is contiguous.
+// Rays per thread of the forward: consecutive detector rows of one column,
+// which share the column's in-plane crossing (f_a, its floor and weight).
+constexpr int FWD_R = 2;
+
+// Narrows [kmin, kmax] to the planes k where f(k) = f0 + (k - cmaj) b lies in
+// [lo, hi], one plane inside the exact bounds on each side (so that FP32
+// rounding of f never leaves [lo, hi] inside the range).
+__device__ __forceinline__ void planes_within(float f0, float b, float lo, float hi, float cmaj, float& kmin,
+                                              float& kmax) {
+    if (fabsf(b) > 1e-12f) {
+        const float k1 = (lo - f0) / b + cmaj, k2 = (hi - f0) / b + cmaj;
+        kmin = fmaxf(kmin, ceilf(fminf(k1, k2)) + 1.0f);
+        kmax = fminf(kmax, floorf(fmaxf(k1, k2)) - 1.0f);
+    } else if (!(f0 >= lo && f0 <= hi)) {
+        kmax = kmin - 1.0f;
+    }
+}
+
+// One thread per FWD_R rays (detector rows FWD_R*i .. FWD_R*i + FWD_R - 1 of one
+// column); a block covers blockDim.x columns x FWD_R*blockDim.y rows of one view
+// (128 threads; the shape is chosen per plan by msf_projector_autotune).  x-major
+// rays read the transposed frame [nz][nx][ny], y-major rays the natural frame
+// [nz][ny][nx], so in both cases the minor in-plane axis is contiguous.  Planes
+// where every bilinear tap of every ray of the thread lies inside the grid run
+// without bounds checks; the planes at either end check each tap.  The
+// interpolation is v00 + w_a (v01 - v00) along a, then the same along z.
 //   FWD_PLAIN:    out = A x
 //   FWD_LAMBDA:   out = step * Lambda * (A x)
 //   FWD_RESIDUAL: out = step * Lambda * (meas - A x)
@@ -162,9 +184,9 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     float* __restrict__ out, const float* __restrict__ lam, const float* __restrict__ meas,
     ProjDims d) {
     const int iu = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
+    const int iv0 = (blockIdx.y * blockDim.y + threadIdx.y) * FWD_R;
     const int g = blockIdx.z;
-    if (iu >= d.nu || iv >= d.nv) return;
+    if (iu >= d.nu || iv0 >= d.nv) return;
     const int t = g / d.views;
     const ColParams c = load_col(col, (size_t)g * d.nu + iu);
     const bool xmaj = c.xmajor != 0.0f;
@@ -172,49 +194,104 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     const size_t fs = (size_t)d.nx * d.ny * d.nz;
     const float* __restrict__ vol = (xmaj ? xT : x) + (size_t)t * fs;
     const float cmaj = xmaj ? d.cx : d.cy;
-    const RayZ rz = ray_z(c, det_v(iv, d), d.cz);
+    const int zs = nmaj * na;    // z stride of the frame
 
-    // planes where the crossing point can touch the grid: -1 < f < n on both
-    // minor axes; computed conservatively (one plane of margin each side)
-    float klo = 0.0f, khi = (float)(nmaj - 1);
-    {
-        const float fm[2] = {c.fa_mid, rz.fz_mid}, bb[2] = {c.ba, rz.bz};
-        const float hi[2] = {(float)na, (float)d.nz};
+    RayZ rz[FWD_R];
+#pragma unroll
+    for (int r = 0; r < FWD_R; ++r) rz[r] = ray_z(c, det_v(min(iv0 + r, d.nv - 1), d), d.cz);
+
+    // planes where some crossing can touch the grid (-1 < f < n on both minor
+    // axes, one plane of margin), and the inner planes where all four taps of
+    // every ray are inside (0.5 <= f <= n - 1.5)
+    float klo = (float)(nmaj - 1), khi = 0.0f;
+    float kin_lo = 0.0f, kin_hi = (float)(nmaj - 1);
+    planes_within(c.fa_mid, c.ba, 0.5f, (float)na - 1.5f, cmaj, kin_lo, kin_hi);
+#pragma unroll
+    for (int r = 0; r < FWD_R; ++r) {
+        float lo = 0.0f, hi = (float)(nmaj - 1);
+        const float fm[2] = {c.fa_mid, rz[r].fz_mid}, bb[2] = {c.ba, rz[r].bz};
+        const float top[2] = {(float)na, (float)d.nz};
         for (int a = 0; a < 2; ++a) {
             if (fabsf(bb[a]) > 1e-12f) {
-                float k1 = (-1.0f - fm[a]) / bb[a] + cmaj, k2 = (hi[a] - fm[a]) / bb[a] + cmaj;
-                klo = fmaxf(klo, floorf(fminf(k1, k2)) - 1.0f);
-                khi = fminf(khi, ceilf(fmaxf(k1, k2)) + 1.0f);
-            } else if (!(fm[a] > -1.0f && fm[a] < hi[a])) {
-                khi = -1.0f;
+                const float k1 = (-1.0f - fm[a]) / bb[a] + cmaj, k2 = (top[a] - fm[a]) / bb[a] + cmaj;
+                lo = fmaxf(lo, floorf(fminf(k1, k2)) - 1.0f);
+                hi = fminf(hi, ceilf(fmaxf(k1, k2)) + 1.0f);
+            } else if (!(fm[a] > -1.0f && fm[a] < top[a])) {
+                hi = -1.0f;
             }
         }
+        if (lo <= hi) {
+            klo = fminf(klo, lo);
+            khi = fmaxf(khi, hi);
+        }
+        planes_within(rz[r].fz_mid, rz[r].bz, 0.5f, (float)d.nz - 1.5f, cmaj, kin_lo, kin_hi);
     }
-    float acc = 0.0f;
-    const int k0 = (int)klo, k1 = (int)khi;
-    for (int k = k0; k <= k1; ++k) {
-        const float tk = __fsub_rn((float)k, cmaj);
-        const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
-        const float fz = __fmaf_rn(tk, rz.bz, rz.fz_mid);
-        const float a0f = floorf(fa), z0f = floorf(fz);
-        const float wa1 = __fsub_rn(fa, a0f), wz1 = __fsub_rn(fz, z0f);
-        const int ia = (int)a0f, iz = (int)z0f;
-        const bool a_in0 = ia >= 0 && ia < na, a_in1 = ia + 1 >= 0 && ia + 1 < na;
-        const bool z_in0 = iz >= 0 && iz < d.nz, z_in1 = iz + 1 >= 0 && iz + 1 < d.nz;
-        const float* row0 = vol + ((ptrdiff_t)iz * nmaj + k) * na;
-        const float* row1 = row0 + (ptrdiff_t)nmaj * na;
-        const float v00 = (z_in0 && a_in0) ? __ldg(row0 + ia) : 0.0f;
-        const float v01 = (z_in0 && a_in1) ? __ldg(row0 + ia + 1) : 0.0f;
-        const float v10 = (z_in1 && a_in0) ? __ldg(row1 + ia) : 0.0f;
-        const float v11 = (z_in1 && a_in1) ? __ldg(row1 + ia + 1) : 0.0f;
-        const float wa0 = __fsub_rn(1.0f, wa1), wz0 = __fsub_rn(1.0f, wz1);
-        acc += wz0 * (wa0 * v00 + wa1 * v01) + wz1 * (wa0 * v10 + wa1 * v11);
+    float acc[FWD_R];
+#pragma unroll
+    for (int r = 0; r < FWD_R; ++r) acc[r] = 0.0f;
+    if (klo <= khi) {
+        const int K0 = (int)klo, K1 = (int)khi;
+        int F0 = (int)fmaxf(kin_lo, klo), F1 = (int)fminf(kin_hi, khi);
+        if (F0 > F1) F0 = K1 + 1, F1 = K1;
+
+        // one plane with every tap checked against the grid
+        auto checked = [&](int k) {
+            const float tk = __fsub_rn((float)k, cmaj);
+            const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
+            const float a0f = floorf(fa);
+            const float wa1 = __fsub_rn(fa, a0f);
+            const int ia = (int)a0f;
+            const bool a_in0 = ia >= 0 && ia < na, a_in1 = ia + 1 >= 0 && ia + 1 < na;
+#pragma unroll
+            for (int r = 0; r < FWD_R; ++r) {
+                const float fz = __fmaf_rn(tk, rz[r].bz, rz[r].fz_mid);
+                const float z0f = floorf(fz);
+                const float wz1 = __fsub_rn(fz, z0f);
+                const int iz = (int)z0f;
+                const bool z_in0 = iz >= 0 && iz < d.nz, z_in1 = iz + 1 >= 0 && iz + 1 < d.nz;
+                const float* row0 = vol + ((ptrdiff_t)iz * nmaj + k) * na;
+                const float* row1 = row0 + zs;
+                const float v00 = (z_in0 && a_in0) ? __ldg(row0 + ia) : 0.0f;
+                const float v01 = (z_in0 && a_in1) ? __ldg(row0 + ia + 1) : 0.0f;
+                const float v10 = (z_in1 && a_in0) ? __ldg(row1 + ia) : 0.0f;
+                const float v11 = (z_in1 && a_in1) ? __ldg(row1 + ia + 1) : 0.0f;
+                const float top = __fmaf_rn(wa1, __fsub_rn(v01, v00), v00);
+                const float bot = __fmaf_rn(wa1, __fsub_rn(v11, v10), v10);
+                acc[r] = __fadd_rn(acc[r], __fmaf_rn(wz1, __fsub_rn(bot, top), top));
+            }
+        };
+        for (int k = K0; k < F0; ++k) checked(k);
+        for (int k = F0; k <= F1; ++k) {
+            const float tk = __fsub_rn((float)k, cmaj);
+            const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
+            const float a0f = floorf(fa);
+            const float wa1 = __fsub_rn(fa, a0f);
+            const float* pk = vol + k * na + (int)a0f;
+#pragma unroll
+            for (int r = 0; r < FWD_R; ++r) {
+                const float fz = __fmaf_rn(tk, rz[r].bz, rz[r].fz_mid);
+                const float z0f = floorf(fz);
+                const float wz1 = __fsub_rn(fz, z0f);
+                const float* p0 = pk + (ptrdiff_t)((int)z0f) * zs;
+                const float* p1 = p0 + zs;
+                const float v00 = __ldg(p0), v01 = __ldg(p0 + 1), v10 = __ldg(p1), v11 = __ldg(p1 + 1);
+                const float top = __fmaf_rn(wa1, __fsub_rn(v01, v00), v00);
+                const float bot = __fmaf_rn(wa1, __fsub_rn(v11, v10), v10);
+                acc[r] = __fadd_rn(acc[r], __fmaf_rn(wz1, __fsub_rn(bot, top), top));
+            }
+        }
+        for (int k = F1 + 1; k <= K1; ++k) checked(k);
     }
-    const float val = acc * rz.step;
-    const size_t ray = ((size_t)g * d.nv + iv) * d.nu + iu;
-    if (MODE == FWD_PLAIN) out[ray] = val;
-    else if (MODE == FWD_LAMBDA) out[ray] = rz.step * (lam[ray] * val);
-    else out[ray] = rz.step * (lam[ray] * (meas[ray] - val));
+#pragma unroll
+    for (int r = 0; r < FWD_R; ++r) {
+        const int iv = iv0 + r;
+        if (iv >= d.nv) break;
+        const float val = acc[r] * rz[r].step;
+        const size_t ray = ((size_t)g * d.nv + iv) * d.nu + iu;
+        if (MODE == FWD_PLAIN) out[ray] = val;
+        else if (MODE == FWD_LAMBDA) out[ray] = rz[r].step * (lam[ray] * val);
+        else out[ray] = rz[r].step * (lam[ray] * (meas[ray] - val));
+    }
 }
 
 // ------------------------------------------------------------------ adjoint (gather)
@@ -240,9 +317,11 @@ __device__ __forceinline__ float u_pixel(float x, float y, float cs, float sn, c
 // iy-1 or iy.  Candidate detector columns come from the exact projection of
 // the segment {x = x_ix, |y - y_iy| <= voxel} (plus one column of margin); on
 // a column that qualifies, the rows whose f_z(k) can fall within one voxel of
-// the run follow from f_z(v) = c_z + v (c1 + tk inv_dmaj).  Each ray's f_a and
-// f_z are then recomputed with the forward's own operations (ray_z, fmaf), so
-// its two z taps and its weights are those of the forward, bit for bit.
+// the run follow from f_z(v) = c_z + v (c1 + tk inv_dmaj).  Each ray's f_a is
+// recomputed with the forward's own operations (bit for bit); f_z of the
+// column's first candidate row likewise, and of the next rows by one FMA along
+// the row (a few 1e-6 voxel from the forward's value, so the taps agree except
+// within that distance of a voxel boundary, where the weights are continuous).
 // Every ray-plane crossing of the forward is visited by the two runs that hold
 // its a-taps, so the work tracks the forward's.
 template <bool XMAJ, int ZB>
@@ -282,9 +361,13 @@ __device__ __forceinline__ void gather_runs(const float4* __restrict__ col, cons
         const int iv_lo = max(0, (int)floorf(va) - 1);
         const int iv_hi = min(d.nv - 1, (int)ceilf(vb) + 1);
         const float* erow = e + ((size_t)g * d.nv) * d.nu + iu;
+        // f_z is affine in the row: the first row's crossing with the forward's
+        // operations, the others one FMA away from it (within a few 1e-6 voxel)
+        const RayZ rz0 = ray_z(c, det_v(iv_lo, d), d.cz);
+        const float fz0 = __fmaf_rn(tk, rz0.bz, rz0.fz_mid);
+        const float dfz = d.dv * __fmaf_rn(tk, c.inv_dmaj, c.c1);
         for (int iv = iv_lo; iv <= iv_hi; ++iv) {
-            const RayZ rz = ray_z(c, det_v(iv, d), d.cz);
-            const float fz = __fmaf_rn(tk, rz.bz, rz.fz_mid);
+            const float fz = __fmaf_rn((float)(iv - iv_lo), dfz, fz0);
             const float z0f = floorf(fz);
             const int k0 = (int)z0f - iz_lo;
             if (k0 < -1 || k0 >= ZB) continue;
@@ -541,12 +624,18 @@ static msf_status launch_transpose(msf_projector* p, const float* in, float* out
     return MSF_OK;
 }
 
+// Forward grid: blockDim.x columns x FWD_R*blockDim.y rows per block, one z per view.
+static dim3 fwd_grid(const ProjDims& d, dim3 block) {
+    const unsigned rows = block.y * FWD_R;
+    return dim3((d.nu + block.x - 1) / block.x, (d.nv + rows - 1) / rows, d.nt * d.views);
+}
+
 static msf_status launch_fwd(msf_projector* p, int mode, const float* x, float* out,
                              const float* lam, const float* meas, cudaStream_t st) {
     MSF_TRY(launch_transpose(p, x, p->d_xT, st));
     const ProjDims& d = p->dims;
     dim3 block(p->fwd_bx, p->fwd_by);
-    dim3 grid((d.nu + block.x - 1) / block.x, (d.nv + block.y - 1) / block.y, d.nt * d.views);
+    dim3 grid = fwd_grid(d, block);
     MSF_PROF("joseph_fwd", st);
     if (mode == FWD_PLAIN)
         joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
@@ -770,7 +859,7 @@ extern "C" msf_status msf_prox_data(msf_dataprox* dp, const float* d_y, const fl
         {   // s = Lambda A p  (transpose already in p->d_xT)
             const ProjDims& d = p->dims;
             dim3 block(p->fwd_bx, p->fwd_by);
-            dim3 grid((d.nu + block.x - 1) / block.x, (d.nv + block.y - 1) / block.y, d.nt * d.views);
+            dim3 grid = fwd_grid(d, block);
             MSF_PROF("joseph_fwd", st);
             joseph_fwd_kernel<FWD_LAMBDA><<<grid, block, 0, st>>>(dp->d_p, p->d_xT, p->d_col, dp->d_s, d_lambda, nullptr, d);
             MSF_LAUNCH_CHECK();
@@ -1013,7 +1102,7 @@ extern "C" msf_status msf_projector_autotune(msf_projector* p, void* stream, int
         const float ms = time_it([&] {
             const ProjDims& d = p->dims;
             dim3 block(p->fwd_bx, p->fwd_by);
-            dim3 grid((d.nu + block.x - 1) / block.x, (d.nv + block.y - 1) / block.y, d.nt * d.views);
+            dim3 grid = fwd_grid(d, block);
             joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(p->d_xT, p->d_xT, p->d_col, tmp, nullptr, nullptr, d);
         });
         if (ms < best) { best = ms; bi = i; }
