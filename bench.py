@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msf", choices=["msf", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "proj", "tiny", "batch"])
+    ap.add_argument("--workload", default="full", choices=["full", "proj", "tiny", "batch", "sweep"])
     ap.add_argument("--no-batch", action="store_true", help="skip the short uneven-batch measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -48,7 +48,7 @@ def parse():
 
 def workload(name):
     from paper_2008_01567_gb300 import synth
-    return {"full": synth.FULL, "proj": synth.PROJ, "tiny": synth.TINY, "batch": synth.FULL}[name]
+    return {"full": synth.FULL, "proj": synth.PROJ, "tiny": synth.TINY, "batch": synth.FULL, "sweep": synth.PROJ}[name]
 
 
 # settings of the plain and learned runs (rho, sigma and agent weights of Eq. (9)).
@@ -331,9 +331,9 @@ def batch_throughput(params, seed, args, dist):
     return res
 
 
-def run_batch(args, rank, world, dist, seed):
-    """--workload batch: the 12 uneven problems, learned vs plain, NRMSE after
-    args.iters iterations and aggregate throughput."""
+def train_small(args, seed):
+    """CNN weights trained on the GPU (args.train_steps Adam steps, batch
+    128 x 5 x 64 x 64) on phantoms of other seeds; returns the flat parameters."""
     import torch
     from paper_2008_01567_gb300 import msf, synth
     tscan = synth.Scan(n=128, nt=4, nu=8, nv=8, views=1)
@@ -348,8 +348,15 @@ def run_batch(args, rank, world, dist, seed):
     for it in range(args.train_steps):
         msf.msf_training_batch(tvols, Pt.vol, 128, 64, 64, 0.02, 0.2, seed * 7919 + it, tn, tc_)
         msf.msf_train_step(cnn, tn, tc_, 1e-3, want_loss=False)
-    params = cnn.get_params()
-    del tvols, tn, tc_, cnn
+    return cnn.get_params()
+
+
+def run_batch(args, rank, world, dist, seed):
+    """--workload batch: the 12 uneven problems, learned vs plain, NRMSE after
+    args.iters iterations and aggregate throughput."""
+    import torch
+    from paper_2008_01567_gb300 import msf, synth
+    params = train_small(args, seed)
     out = {}
     for name, learned in (("learned", True), ("plain", False)):
         items = make_batch(params, seed, learned)
@@ -377,6 +384,77 @@ def run_batch(args, rank, world, dist, seed):
                 "config": {"workload": f"{n} uneven 4D problems 64^3x4..192^3x12, 16..48 views, 360/90 deg, "
                                        "one captured graph per batch iteration"},
                 "learned": out["learned"], "plain": out["plain"]}
+        print(json.dumps(line))
+    return None
+
+
+# ---------------------------------------------------------------- sparse-view / limited-angle sweep
+
+SWEEP = [(90, 4), (180, 8), (360, 16)]   # degrees turned and views per time-point (22.5 deg apart)
+
+
+def run_sweep(args, rank, world, dist, seed):
+    """--workload sweep: Sec. VI's extreme sparse-view study (90/180/360 deg per
+    time-point with 4/8/16 views, continuous rotation) at 128^3 x 8 on a 192 x 160
+    detector, and its single-plane comparison: for each scan, MACE with the plain
+    q-GGMRF prior, multi-slice fusion (three CNN agents) and MBIR + H_xy,t /
+    H_yz,t / H_zx,t (one CNN agent, K = 1), args.iters iterations each; NRMSE,
+    PSNR and SSIM against the phantom, and iterations/s."""
+    import torch
+    from paper_2008_01567_gb300 import metrics, msf, synth
+    params = train_small(args, seed)
+    rows = []
+    for deg, views in SWEEP:
+        scan = synth.Scan(n=128, nt=8, nu=192, nv=160, views=views, mode=f"wedge{deg}")
+        prob = make_problem(scan, seed + deg)
+        msf.msf_projector_autotune(prob["P"])
+        shape3 = (scan.nt, scan.n, scan.n, scan.n)
+        cnn = msf.Cnn(scan.n ** 3)
+        cnn.set_params(params)
+        # multi-slice fusion twice: equal weights 0.25 (beta = 3, as in the
+        # full workload) and beta = 1, which gives the data agent the weight 0.5
+        # it has in the single-CNN runs (mu_0 = 1/(1+beta), mu_k = beta/((1+beta)K))
+        methods = [("plain q-GGMRF", 1, None), ("multi-slice fusion", 3, None),
+                   ("multi-slice fusion, beta=1", 3, None)] + \
+                  [(f"MBIR + H_{o},t", 1, k) for k, o in enumerate(("xy", "yz", "zx"))]
+        for name, K, orient in methods:
+            W = torch.zeros((K + 1,) + shape3, device="cuda")
+            X = torch.zeros_like(W)
+            if name.startswith("plain"):
+                s = PLAIN
+                m = msf.Mace(prob["P"], W, X, prob["y"], prob["lam"], msf.MSF_PRIOR_QGGMRF,
+                             mrf=msf.msf_mrf(2.0, s["q"], s["T"], s["sx"], s["bt"]))
+                prm = (s["rho"], s["sigma"], s["mu"], s["n_cg"], s["n_sweeps"])
+            else:
+                mu = [0.5, 0.5] if K == 1 else ([0.5] + [1.0 / 6] * 3 if "beta=1" in name else LEARNED["mu"])
+                m = msf.Mace(prob["P"], W, X, prob["y"], prob["lam"], msf.MSF_PRIOR_CNN, cnn=cnn,
+                             orient=orient or 0)
+                prm = (LEARNED["rho"], LEARNED["sigma"], mu, LEARNED["n_cg"], 0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.iters):
+                msf.msf_mace_step(m, *prm, want_residual=False, use_graph=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            x, ref = X[0], prob["x_true"]
+            rows.append({"degrees": deg, "views": views, "method": name, "iters": args.iters,
+                         "iters_per_s": args.iters / dt, "nrmse": round(metrics.nrmse(x, ref), 4),
+                         "psnr_db": round(metrics.psnr(x, ref), 2), "ssim": round(metrics.ssim(x, ref), 4)})
+            m.close()
+            del W, X, m
+        del cnn, prob
+    if rank == 0:
+        best = {(r["degrees"], r["views"]): max((q for q in rows if q["degrees"] == r["degrees"]),
+                                                key=lambda q: q["psnr_db"])["method"] for r in rows}
+        msf_rows = [r for r in rows if r["method"] == "multi-slice fusion"]
+        line = {"metric": METRIC, "value": msf_rows[-1]["iters_per_s"], "unit": "MACE iters/s",
+                "n_gpus": world, "steps": args.iters, "warmup": 0,
+                "ms_per_step": 1e3 / msf_rows[-1]["iters_per_s"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 (CNN agents), f32 (projector, CG, consensus), f64 (scalars)",
+                "data": "synthetic (seeded moving-ellipsoid phantoms, Poisson 1e4; CNN trained on GPU-generated pairs)",
+                "config": {"workload": "sparse-view / limited-angle sweep 128^3x8, det 192x160, "
+                                       "90/180/360 deg per time-point with 4/8/16 views"},
+                "sweep": rows, "best_psnr": {f"{d}deg/{v}views": m for (d, v), m in best.items()}}
         print(json.dumps(line))
     return None
 
@@ -423,6 +501,8 @@ def main():
     seed = replica_seed(rank)
     if args.workload == "batch":
         return run_batch(args, rank, world, dist, seed)
+    if args.workload == "sweep":
+        return run_sweep(args, rank, world, dist, seed)
     prob = make_problem(scan, seed)
     P = prob["P"]
     tuned = msf.msf_projector_autotune(P)
@@ -499,7 +579,10 @@ def main():
     # the same iteration replayed as one CUDA graph
     gms = timed(lambda: msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0, want_residual=False,
                                           use_graph=True), args.steps, 1, dist)
+    from paper_2008_01567_gb300 import metrics
     learned = {"iters_per_s": value, "graph_iters_per_s": world * args.steps / (gms / 1e3), "nrmse": nrmse(X[0]),
+               "psnr_db": round(metrics.psnr(X[0], prob["x_true"]), 2),
+               "ssim": round(metrics.ssim(X[0], prob["x_true"]), 4),
                "residual": res, "iters": done + 1 + args.steps + 1}
     del m, W, X
     batch = None
@@ -523,7 +606,9 @@ def main():
         pstep()
     pres = msf.msf_mace_step(m2, s["rho"], s["sigma"], s["mu"], s["n_cg"], s["n_sweeps"])
     plain = {"iters_per_s": world * args.steps / (pms / 1e3), "ms_per_iter": pms / args.steps,
-             "nrmse": nrmse(X2[0]), "residual": pres, "iters": total_iters + 1, "sigma_x": s["sx"]}
+             "nrmse": nrmse(X2[0]), "psnr_db": round(metrics.psnr(X2[0], prob["x_true"]), 2),
+             "ssim": round(metrics.ssim(X2[0], prob["x_true"]), 4),
+             "residual": pres, "iters": total_iters + 1, "sigma_x": s["sx"]}
     del m2, W2, X2
 
     # ---------------- projector throughput (one launch each, algorithmic bytes)

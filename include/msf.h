@@ -264,9 +264,12 @@ typedef enum { MSF_PRIOR_QGGMRF = 0, MSF_PRIOR_CNN = 1 } msf_prior_kind;
 
 typedef struct msf_mace msf_mace;
 
-/* A MACE problem.  K prior agents: with MSF_PRIOR_CNN, K = 3 and the agents
- * are H_xy,t, H_yz,t, H_zx,t sharing `cnn` (Eq. (14)); with MSF_PRIOR_QGGMRF,
- * K = 1 and the agent is the q-GGMRF prox with `mrf`.  d_W and d_X hold the
+/* A MACE problem.  K prior agents: with MSF_PRIOR_CNN and K = 3 the agents
+ * are H_xy,t, H_yz,t, H_zx,t sharing `cnn` (Eq. (14)); with MSF_PRIOR_CNN and
+ * K = 1 the single agent is the CNN of orientation `orient` (the "MBIR + H" PnP
+ * comparison of Sec. VI: one CNN prior beside the data agent); with
+ * MSF_PRIOR_QGGMRF, K = 1 and the agent is the q-GGMRF prox with `mrf`.
+ * `orient` is read only for the single-CNN case.  d_W and d_X hold the
  * K+1 stacked states [K+1][nt][nz][ny][nx] (caller-owned, initialised by the
  * caller; Algorithm 1 starts from W = X = [x0; ...; x0]).  d_y, d_lambda: the
  * measurements and weights.  The handle borrows proj and cnn. */
@@ -280,6 +283,7 @@ typedef struct {
     float* d_X;
     const float* d_y;
     const float* d_lambda;
+    msf_orient orient;
 } msf_mace_desc;
 
 typedef struct {

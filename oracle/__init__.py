@@ -271,6 +271,45 @@ def psnr(x, ref):
     return 20.0 * math.log10(rng / math.sqrt(float(np.mean((x - ref) ** 2))))
 
 
+def ssim_map2d(a, b, L, win=11, sd=1.5, k1=0.01, k2=0.03):
+    """SSIM map of two 2D images (Wang et al.): local means, variances and
+    covariance under a normalised win x win Gaussian window (standard deviation
+    sd), at every window position wholly inside the image, combined as
+    (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
+    C1 = (k1 L)^2, C2 = (k2 L)^2.  Written as the windowed sums themselves."""
+    r = np.arange(win) - (win - 1) / 2.0
+    g1 = np.exp(-r * r / (2.0 * sd * sd))
+    w = np.outer(g1, g1)
+    w /= w.sum()
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    H, W = a.shape
+    out = np.empty((H - win + 1, W - win + 1))
+    c1, c2 = (k1 * L) ** 2, (k2 * L) ** 2
+    for i in range(H - win + 1):
+        for j in range(W - win + 1):
+            pa = a[i:i + win, j:j + win]
+            pb = b[i:i + win, j:j + win]
+            mx, my = float((w * pa).sum()), float((w * pb).sum())
+            sxx = float((w * (pa - mx) ** 2).sum())
+            syy = float((w * (pb - my) ** 2).sum())
+            sxy = float((w * (pa - mx) * (pb - my)).sum())
+            out[i, j] = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+    return out
+
+
+def ssim(x, ref, L=None):
+    """Mean SSIM over every 2D slice of the last two axes (xy-slices of each
+    time-point of a 4D volume); L defaults to the PSNR's percentile range of ref."""
+    if L is None:
+        L = np.percentile(ref, 99.9) - np.percentile(ref, 0.1)
+    H, W = ref.shape[-2:]
+    xs = np.asarray(x, dtype=np.float64).reshape(-1, H, W)
+    rs = np.asarray(ref, dtype=np.float64).reshape(-1, H, W)
+    maps = [ssim_map2d(a, b, L) for a, b in zip(xs, rs)]
+    return float(np.mean(np.stack(maps)))
+
+
 # ====================================================================== Sec. IV-V
 # 2.5D CNN denoiser: five adjacent time-points of a 2D slice enter as channels and
 # the denoised centre slice comes out, with a residual connection through the

@@ -174,7 +174,8 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
         if (d.prior == MSF_PRIOR_QGGMRF) {
             MSF_TRY(msf_prox_qggmrf(vol, &d.mrf, d.d_W + k * N, d.d_X + k * N, prm->sigma, prm->n_sweeps, sv));
         } else {
-            MSF_TRY(msf_denoise(d.cnn, (msf_orient)(k - 1), vol, d.d_W + k * N, d.d_X + k * N, sv));
+            const msf_orient o = d.K == 1 ? d.orient : (msf_orient)(k - 1);
+            MSF_TRY(msf_denoise(d.cnn, o, vol, d.d_W + k * N, d.d_X + k * N, sv));
         }
     }
     // Z <- G(2X - W);  W <- W + 2 rho (Z - X)
@@ -262,7 +263,10 @@ extern "C" msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out)
     MSF_REQUIRE(desc->proj && desc->d_W && desc->d_X && desc->d_y && desc->d_lambda,
                 "msf_mace_create: projector, W, X, y and lambda are required");
     if (desc->prior == MSF_PRIOR_CNN) {
-        MSF_REQUIRE(desc->K == 3 && desc->cnn, "msf_mace_create: the CNN prior needs K = 3 and a cnn handle");
+        MSF_REQUIRE((desc->K == 3 || desc->K == 1) && desc->cnn,
+                    "msf_mace_create: the CNN prior needs K = 3 (or K = 1) and a cnn handle");
+        MSF_REQUIRE(desc->K == 3 || (desc->orient >= MSF_XY_T && desc->orient <= MSF_ZX_T),
+                    "msf_mace_create: bad orientation %d for the single CNN agent", (int)desc->orient);
     } else if (desc->prior == MSF_PRIOR_QGGMRF) {
         MSF_REQUIRE(desc->K == 1, "msf_mace_create: the q-GGMRF prior uses K = 1");
         MSF_REQUIRE(desc->mrf.p == 2.0 && desc->mrf.q >= 1.0 && desc->mrf.q <= 2.0 && desc->mrf.T > 0 &&

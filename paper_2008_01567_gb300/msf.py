@@ -47,7 +47,8 @@ class msf_mrf(ctypes.Structure):
 class msf_mace_desc(ctypes.Structure):
     _fields_ = [("proj", ctypes.c_void_p), ("prior", ctypes.c_int), ("K", ctypes.c_int),
                 ("cnn", ctypes.c_void_p), ("mrf", msf_mrf), ("d_W", ctypes.c_void_p),
-                ("d_X", ctypes.c_void_p), ("d_y", ctypes.c_void_p), ("d_lambda", ctypes.c_void_p)]
+                ("d_X", ctypes.c_void_p), ("d_y", ctypes.c_void_p), ("d_lambda", ctypes.c_void_p),
+                ("orient", ctypes.c_int)]
 
 
 class msf_mace_params(ctypes.Structure):
@@ -338,11 +339,13 @@ class Mace:
     """Owns an msf_mace handle over caller tensors W, X [K+1, nt, nz, ny, nx]."""
 
     def __init__(self, proj: Projector, W, X, y, lam, prior: int, mrf: msf_mrf | None = None,
-                 cnn: Cnn | None = None):
+                 cnn: Cnn | None = None, orient: int = 0):
+        """K = W.shape[0] - 1 prior agents; with the CNN prior and K = 1 the
+        single agent is the CNN of orientation `orient` (0 xy-t, 1 yz-t, 2 zx-t)."""
         K = W.shape[0] - 1
         self.desc = msf_mace_desc(proj.handle, prior, K, cnn.handle if cnn else None,
                                   mrf if mrf is not None else msf_mrf(2.0, 1.2, 1.0, 1.0, 0.5),
-                                  _f32(W), _f32(X), _f32(y), _f32(lam))
+                                  _f32(W), _f32(X), _f32(y), _f32(lam), orient)
         self._keep = (proj, W, X, y, lam, cnn)
         h = ctypes.c_void_p()
         _check(lib().msf_mace_create(ctypes.byref(self.desc), ctypes.byref(h)))

@@ -36,7 +36,7 @@ class Scan:
     nu: int
     nv: int
     views: int
-    mode: str = "sparse360"  # or "wedge90"
+    mode: str = "sparse360"  # or "wedge<D>", e.g. "wedge90"
     dso: float = 4.0          # source to rotation axis
     dsd: float = 8.0          # source to detector (magnification 2)
 
@@ -59,15 +59,19 @@ class Scan:
 
         sparse360: each frame's views span 360 deg and are interlaced across
         frames, th = 2 pi (j + t/nt) / views.
-        wedge90: the object turns continuously; frame t covers the 90 deg wedge
-        [t pi/2, (t+1) pi/2), th = (pi/2) (t + j/views).
+        wedge<D> (e.g. wedge90, wedge180, wedge360): the object turns
+        continuously and frame t covers the D-degree wedge [t W, (t+1) W),
+        W = D pi / 180, with th = W (t + j/views).
         """
         t = np.arange(self.nt, dtype=np.float64)[:, None]
         j = np.arange(self.views, dtype=np.float64)[None, :]
         if self.mode == "sparse360":
             return 2.0 * math.pi * (j + t / self.nt) / self.views
-        if self.mode == "wedge90":
-            return 0.5 * math.pi * (t + j / self.views)
+        if self.mode.startswith("wedge"):
+            deg = float(self.mode[len("wedge"):])
+            if not 0.0 < deg <= 360.0:
+                raise ValueError(self.mode)
+            return math.radians(deg) * (t + j / self.views)
         raise ValueError(self.mode)
 
 

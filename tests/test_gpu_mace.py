@@ -119,6 +119,55 @@ def test_learned_mace_matches_oracle(M):
     np.testing.assert_allclose(res_gpu, res, rtol=2e-2)
 
 
+@pytest.mark.parametrize("orient", [0, 2])
+def test_single_cnn_pnp_matches_oracle(M, orient):
+    # The "MBIR + H" comparison of Sec. VI: the data agent and one CNN prior of
+    # one orientation (K = 1), weights 0.5 / 0.5 (beta = 1).  Same bound as the
+    # three-agent case.
+    import torch
+    scan = synth.TINY
+    x0, counts, y, lam = measurement(scan, 45)
+    sigma, rho, n_cg, iters = 0.1, 0.8, 5, 3
+    mu = [0.5, 0.5]
+    convs, bns, stats = _cnn_net(46)
+    cnn = M.Cnn(scan.n ** 3)
+    flat = M.pack_params(convs, bns, stats)
+    cnn.set_params(flat)
+    layers = oracle.fold_bn(*M.unpack_params(flat))
+    P = M.Projector(scan)
+    c = _t(counts)
+    yg, lg = torch.empty_like(c), torch.empty_like(c)
+    M.msf_weights(c, yg, lg, I0, I0)
+    shape = (2, scan.nt, scan.n, scan.n, scan.n)
+    W = torch.zeros(shape, device="cuda")
+    X = torch.zeros(shape, device="cuda")
+    m = M.Mace(P, W, X, yg, lg, M.MSF_PRIOR_CNN, cnn=cnn, orient=orient)
+    res_gpu = [M.msf_mace_step(m, rho, sigma, mu, n_cg) for _ in range(iters)]
+    yf, lf = f32(y), f32(lam)
+    o = oracle.ORIENTS[orient]
+    agents = [lambda w, x: oracle.prox_data(yf, lf, w, x, scan, sigma, n_cg),
+              lambda w, x: oracle.denoise(w, layers, o, emulate_bf16=True)]
+    xhat, Wo, Xo, res = oracle.mace(np.zeros(shape[1:]), agents, mu, rho, iters)
+    assert rel_l2(X[0].cpu().numpy(), xhat) <= 1e-2
+    assert rel_l2(W.cpu().numpy(), np.stack(Wo)) <= 1e-2
+    np.testing.assert_allclose(res_gpu, res, rtol=2e-2)
+
+
+def test_single_cnn_agent_arguments(M):
+    import torch
+    scan = synth.TINY
+    P = M.Projector(scan)
+    cnn = M.Cnn(scan.n ** 3)
+    y = torch.zeros((scan.nt, scan.views, scan.nv, scan.nu), device="cuda")
+    W = torch.zeros((2, scan.nt, scan.n, scan.n, scan.n), device="cuda")
+    X = torch.zeros_like(W)
+    with pytest.raises(M.MsfError):
+        M.Mace(P, W, X, y, y, M.MSF_PRIOR_CNN, cnn=cnn, orient=3)
+    W3 = torch.zeros((3, scan.nt, scan.n, scan.n, scan.n), device="cuda")
+    with pytest.raises(M.MsfError):          # K = 2 is neither form
+        M.Mace(P, W3, torch.zeros_like(W3), y, y, M.MSF_PRIOR_CNN, cnn=cnn)
+
+
 def _train(M, cnn, vols, vol, steps, seed, B=32, H=48, W=48, lr=1e-3):
     import torch
     cnn.train_reserve(B * H * W)
