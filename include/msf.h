@@ -101,7 +101,8 @@ typedef struct msf_projector msf_projector;
  * would lie inside the volume's circumscribed cylinder (dso and dsd-dso must
  * exceed its radius), or when a ray could be steeper than 45 deg to the
  * rotation plane (the z-major case, which this projector does not model).
- * Allocates the table plus one transposed frame stack (4*N bytes). */
+ * Allocates the table, two z-paired copies of a 4D volume (the forward's
+ * inputs, 16*N bytes) and a step-weighted sinogram. */
 msf_status msf_projector_create(const msf_geom* geom, const msf_vol* vol, msf_projector** out);
 void msf_projector_destroy(msf_projector* p);
 /* Device bytes held by the plan. */

@@ -106,19 +106,24 @@ __global__ void column_table_kernel(const double* __restrict__ angles, float4* _
     (void)na;
 }
 
-// ------------------------------------------------------------------ transpose
+// ------------------------------------------------------------------ z-paired copies
 
-// Per frame and z-slice: out[x][y] = in[y][x] (x-major rays read the frame with
-// y contiguous).  FUSED: p <- r + beta_t p, written back and transposed (the
-// CG direction update folded into the transpose of the next forward pass).
+// Per frame and z-slice, the two copies of a volume v that the forward reads:
+// py[z][y][x] = (v(z, y, x), v(z + 1, y, x)) and px[z][x][y], the same pairs
+// transposed (x-major rays read y-contiguous data), with v(nz, ., .) = 0, so
+// that a ray's four bilinear taps are two 8-byte loads.
+// FUSED: v = r + beta_t p (the CG direction update) with p = in; v is also
+// written to pnext (a different buffer: neighbouring slices still read p).
 template <bool FUSED>
-__global__ void transpose_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                 const float* __restrict__ r, float* __restrict__ p,
-                                 const double* __restrict__ beta, int nx, int ny, int nz) {
-    __shared__ float tile[32][33];
+__global__ void pair_kernel(const float* __restrict__ in, float2* __restrict__ px, float2* __restrict__ py,
+                            const float* __restrict__ r, float* __restrict__ pnext, const double* __restrict__ beta,
+                            int nx, int ny, int nz) {
+    __shared__ float2 tile[32][33];
     const int slice = blockIdx.z;             // t * nz + z
-    const int t = slice / nz;
-    const size_t base = (size_t)slice * nx * ny;
+    const int t = slice / nz, z = slice % nz;
+    const size_t plane = (size_t)nx * ny;
+    const size_t base = (size_t)slice * plane;
+    const bool up = z + 1 < nz;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
     float bt = 0.0f;
     if (FUSED) bt = (float)beta[t];
@@ -126,20 +131,24 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
         const int x = x0 + threadIdx.x, y = y0 + k;
         if (x < nx && y < ny) {
             const size_t i = base + (size_t)y * nx + x;
-            float val;
+            float lo, hi = 0.0f;
             if (FUSED) {
-                val = __fmaf_rn(bt, p[i], r[i]);
-                p[i] = val;
+                lo = __fmaf_rn(bt, in[i], r[i]);
+                if (up) hi = __fmaf_rn(bt, in[i + plane], r[i + plane]);
+                pnext[i] = lo;
             } else {
-                val = in[i];
+                lo = in[i];
+                if (up) hi = in[i + plane];
             }
-            tile[k][threadIdx.x] = val;
+            const float2 v = make_float2(lo, hi);
+            py[i] = v;
+            tile[k][threadIdx.x] = v;
         }
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int y = y0 + threadIdx.x, x = x0 + k;
-        if (x < nx && y < ny) out[base + (size_t)x * ny + y] = tile[threadIdx.x][k];
+        if (x < nx && y < ny) px[base + (size_t)x * ny + y] = tile[threadIdx.x][k];
     }
 }
 
@@ -168,8 +177,9 @@ __device__ __forceinline__ void planes_within(float f0, float b, float lo, float
 // One thread per FWD_R rays (detector rows FWD_R*i .. FWD_R*i + FWD_R - 1 of one
 // column); a block covers blockDim.x columns x FWD_R*blockDim.y rows of one view
 // (128 threads; the shape is chosen per plan by msf_projector_autotune).  x-major
-// rays read the transposed frame [nz][nx][ny], y-major rays the natural frame
-// [nz][ny][nx], so in both cases the minor in-plane axis is contiguous.  Planes
+// rays read the z-paired transposed frame px [nz][nx][ny], y-major rays the
+// z-paired natural frame py [nz][ny][nx] (pair_kernel), so the minor in-plane
+// axis is contiguous and each (a, z) tap pair is one 8-byte load.  Planes
 // where every bilinear tap of every ray of the thread lies inside the grid run
 // without bounds checks; the planes at either end check each tap.  The
 // interpolation is v00 + w_a (v01 - v00) along a, then the same along z.
@@ -180,7 +190,7 @@ __device__ __forceinline__ void planes_within(float f0, float b, float lo, float
 // adjoint consumes)
 template <int MODE>
 __global__ void __launch_bounds__(128) joseph_fwd_kernel(
-    const float* __restrict__ x, const float* __restrict__ xT, const float4* __restrict__ col,
+    const float2* __restrict__ px, const float2* __restrict__ py, const float4* __restrict__ col,
     float* __restrict__ out, const float* __restrict__ lam, const float* __restrict__ meas,
     ProjDims d) {
     const int iu = blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,7 +202,7 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     const bool xmaj = c.xmajor != 0.0f;
     const int nmaj = xmaj ? d.nx : d.ny, na = xmaj ? d.ny : d.nx;
     const size_t fs = (size_t)d.nx * d.ny * d.nz;
-    const float* __restrict__ vol = (xmaj ? xT : x) + (size_t)t * fs;
+    const float2* __restrict__ vol = (xmaj ? px : py) + (size_t)t * fs;   // (v(z), v(z+1)) pairs
     const float cmaj = xmaj ? d.cx : d.cy;
     const int zs = nmaj * na;    // z stride of the frame
 
@@ -248,13 +258,18 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
                 const float z0f = floorf(fz);
                 const float wz1 = __fsub_rn(fz, z0f);
                 const int iz = (int)z0f;
-                const bool z_in0 = iz >= 0 && iz < d.nz, z_in1 = iz + 1 >= 0 && iz + 1 < d.nz;
-                const float* row0 = vol + ((ptrdiff_t)iz * nmaj + k) * na;
-                const float* row1 = row0 + zs;
-                const float v00 = (z_in0 && a_in0) ? __ldg(row0 + ia) : 0.0f;
-                const float v01 = (z_in0 && a_in1) ? __ldg(row0 + ia + 1) : 0.0f;
-                const float v10 = (z_in1 && a_in0) ? __ldg(row1 + ia) : 0.0f;
-                const float v11 = (z_in1 && a_in1) ? __ldg(row1 + ia + 1) : 0.0f;
+                // the pair of slice iz holds taps iz and iz + 1 (0 above the
+                // grid); below it (iz = -1) only the upper tap, from slice 0
+                float v00 = 0.0f, v01 = 0.0f, v10 = 0.0f, v11 = 0.0f;
+                if (iz >= 0 && iz < d.nz) {
+                    const float2* row = vol + ((ptrdiff_t)iz * nmaj + k) * na;
+                    if (a_in0) { const float2 q = __ldg(row + ia); v00 = q.x; v10 = q.y; }
+                    if (a_in1) { const float2 q = __ldg(row + ia + 1); v01 = q.x; v11 = q.y; }
+                } else if (iz == -1) {
+                    const float2* row = vol + (ptrdiff_t)k * na;
+                    if (a_in0) v10 = __ldg(row + ia).x;
+                    if (a_in1) v11 = __ldg(row + ia + 1).x;
+                }
                 const float top = __fmaf_rn(wa1, __fsub_rn(v01, v00), v00);
                 const float bot = __fmaf_rn(wa1, __fsub_rn(v11, v10), v10);
                 acc[r] = __fadd_rn(acc[r], __fmaf_rn(wz1, __fsub_rn(bot, top), top));
@@ -266,15 +281,15 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
             const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
             const float a0f = floorf(fa);
             const float wa1 = __fsub_rn(fa, a0f);
-            const float* pk = vol + k * na + (int)a0f;
+            const float2* pk = vol + k * na + (int)a0f;
 #pragma unroll
             for (int r = 0; r < FWD_R; ++r) {
                 const float fz = __fmaf_rn(tk, rz[r].bz, rz[r].fz_mid);
                 const float z0f = floorf(fz);
                 const float wz1 = __fsub_rn(fz, z0f);
-                const float* p0 = pk + (ptrdiff_t)((int)z0f) * zs;
-                const float* p1 = p0 + zs;
-                const float v00 = __ldg(p0), v01 = __ldg(p0 + 1), v10 = __ldg(p1), v11 = __ldg(p1 + 1);
+                const float2* p0 = pk + (ptrdiff_t)((int)z0f) * zs;
+                const float2 q0 = __ldg(p0), q1 = __ldg(p0 + 1);
+                const float v00 = q0.x, v10 = q0.y, v01 = q1.x, v11 = q1.y;
                 const float top = __fmaf_rn(wa1, __fsub_rn(v01, v00), v00);
                 const float bot = __fmaf_rn(wa1, __fsub_rn(v11, v10), v10);
                 acc[r] = __fadd_rn(acc[r], __fmaf_rn(wz1, __fsub_rn(bot, top), top));
@@ -591,7 +606,8 @@ struct msf_projector {
     float4* d_col = nullptr;
     float2* d_trig = nullptr;
     int* d_vflag = nullptr;
-    float* d_xT = nullptr;
+    float2* d_px = nullptr;    // z-paired volume, [nt][nz][nx][ny] (x-major rays)
+    float2* d_py = nullptr;    // z-paired volume, [nt][nz][ny][nx] (y-major rays)
     float* d_sw = nullptr;     // step-weighted sinogram for msf_backproject
     int fwd_bx = 32, fwd_by = 4;   // forward ray block (columns x rows)
     int adj_zb = 16;               // gather z-run length
@@ -600,7 +616,7 @@ struct msf_projector {
 
 struct msf_dataprox {
     msf_projector* p = nullptr;
-    float *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_s = nullptr;
+    float *d_r = nullptr, *d_p = nullptr, *d_p2 = nullptr, *d_q = nullptr, *d_s = nullptr;
     double *d_partial = nullptr, *d_rr = nullptr, *d_alpha = nullptr, *d_beta = nullptr;
     int* d_status = nullptr;
     int parts_adj = 0, parts_upd = 0, parts_max = 0;
@@ -614,12 +630,11 @@ static size_t sino_size(const msf_projector* p) {
     return (size_t)p->geom.nu * p->geom.nv * p->geom.views * p->vol.nt;
 }
 
-static msf_status launch_transpose(msf_projector* p, const float* in, float* out, cudaStream_t st) {
+static msf_status launch_pairs(msf_projector* p, const float* in, cudaStream_t st) {
     const msf_vol& v = p->vol;
     dim3 grid((v.nx + 31) / 32, (v.ny + 31) / 32, v.nz * v.nt);
     MSF_PROF("transpose", st);
-    transpose_kernel<false><<<grid, dim3(32, 8), 0, st>>>(in, out, nullptr, nullptr, nullptr, v.nx,
-                                                          v.ny, v.nz);
+    pair_kernel<false><<<grid, dim3(32, 8), 0, st>>>(in, p->d_px, p->d_py, nullptr, nullptr, nullptr, v.nx, v.ny, v.nz);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
 }
@@ -632,17 +647,17 @@ static dim3 fwd_grid(const ProjDims& d, dim3 block) {
 
 static msf_status launch_fwd(msf_projector* p, int mode, const float* x, float* out,
                              const float* lam, const float* meas, cudaStream_t st) {
-    MSF_TRY(launch_transpose(p, x, p->d_xT, st));
+    MSF_TRY(launch_pairs(p, x, st));
     const ProjDims& d = p->dims;
     dim3 block(p->fwd_bx, p->fwd_by);
     dim3 grid = fwd_grid(d, block);
     MSF_PROF("joseph_fwd", st);
     if (mode == FWD_PLAIN)
-        joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
+        joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(p->d_px, p->d_py, p->d_col, out, lam, meas, d);
     else if (mode == FWD_LAMBDA)
-        joseph_fwd_kernel<FWD_LAMBDA><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
+        joseph_fwd_kernel<FWD_LAMBDA><<<grid, block, 0, st>>>(p->d_px, p->d_py, p->d_col, out, lam, meas, d);
     else
-        joseph_fwd_kernel<FWD_RESIDUAL><<<grid, block, 0, st>>>(x, p->d_xT, p->d_col, out, lam, meas, d);
+        joseph_fwd_kernel<FWD_RESIDUAL><<<grid, block, 0, st>>>(p->d_px, p->d_py, p->d_col, out, lam, meas, d);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
 }
@@ -729,12 +744,12 @@ extern "C" msf_status msf_projector_create(const msf_geom* geom, const msf_vol* 
         cudaMalloc(&p->d_col, col_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_trig, G * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&p->d_vflag, G * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&p->d_xT, vol_bytes) != cudaSuccess ||
+        cudaMalloc(&p->d_px, 2 * vol_bytes) != cudaSuccess || cudaMalloc(&p->d_py, 2 * vol_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_sw, sino_size(p) * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(MSF_ERR_NOMEM, "msf_projector_create: out of device memory"));
     }
-    p->bytes = G * sizeof(double) + col_bytes + G * (sizeof(float2) + sizeof(int)) + vol_bytes +
+    p->bytes = G * sizeof(double) + col_bytes + G * (sizeof(float2) + sizeof(int)) + 4 * vol_bytes +
                sino_size(p) * sizeof(float);
     std::vector<float2> trig(G);
     for (int g = 0; g < G; ++g) trig[g] = make_float2((float)cos(p->angles[g]), (float)sin(p->angles[g]));
@@ -765,7 +780,8 @@ extern "C" void msf_projector_destroy(msf_projector* p) {
     cudaFree(p->d_col);
     cudaFree(p->d_trig);
     cudaFree(p->d_vflag);
-    cudaFree(p->d_xT);
+    cudaFree(p->d_px);
+    cudaFree(p->d_py);
     cudaFree(p->d_sw);
     delete p;
 }
@@ -802,6 +818,7 @@ extern "C" msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out) 
     d->parts_max = d->parts_adj > d->parts_upd ? d->parts_adj : d->parts_upd;
     const int nt = p->vol.nt;
     if (cudaMalloc(&d->d_r, nv * 4) != cudaSuccess || cudaMalloc(&d->d_p, nv * 4) != cudaSuccess ||
+        cudaMalloc(&d->d_p2, nv * 4) != cudaSuccess ||
         cudaMalloc(&d->d_q, nv * 4) != cudaSuccess || cudaMalloc(&d->d_s, ns * 4) != cudaSuccess ||
         cudaMalloc(&d->d_partial, (size_t)nt * d->parts_max * 8) != cudaSuccess ||
         cudaMalloc(&d->d_rr, nt * 8) != cudaSuccess || cudaMalloc(&d->d_alpha, nt * 8) != cudaSuccess ||
@@ -820,7 +837,7 @@ extern "C" msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out) 
 
 extern "C" void msf_dataprox_destroy(msf_dataprox* d) {
     if (!d) return;
-    cudaFree(d->d_r); cudaFree(d->d_p); cudaFree(d->d_q); cudaFree(d->d_s);
+    cudaFree(d->d_r); cudaFree(d->d_p); cudaFree(d->d_p2); cudaFree(d->d_q); cudaFree(d->d_s);
     cudaFree(d->d_partial); cudaFree(d->d_rr); cudaFree(d->d_alpha); cudaFree(d->d_beta);
     cudaFree(d->d_status);
     delete d;
@@ -847,25 +864,31 @@ extern "C" msf_status msf_prox_data(msf_dataprox* dp, const float* d_y, const fl
     }
     const msf_vol& v = p->vol;
     const dim3 tgrid((v.nx + 31) / 32, (v.ny + 31) / 32, v.nz * v.nt);
+    // the direction p alternates between two buffers: the fused update reads
+    // p at slices z and z + 1 while writing the new p
+    float* pc = dp->d_p;
     for (int it = 0; it < n_cg; ++it) {
-        // p^T for the forward pass (fused with p = r + beta p after the first pass)
+        // z-paired copies of p for the forward pass (fused with p = r + beta p after the first pass)
         if (it == 0) {
-            MSF_TRY(launch_transpose(p, dp->d_p, p->d_xT, st));
+            MSF_TRY(launch_pairs(p, pc, st));
         } else {
+            float* pn = pc == dp->d_p ? dp->d_p2 : dp->d_p;
             MSF_PROF("transpose_pupdate", st);
-            transpose_kernel<true><<<tgrid, dim3(32, 8), 0, st>>>(nullptr, p->d_xT, dp->d_r, dp->d_p, dp->d_beta, v.nx, v.ny, v.nz);
+            pair_kernel<true><<<tgrid, dim3(32, 8), 0, st>>>(pc, p->d_px, p->d_py, dp->d_r, pn, dp->d_beta, v.nx,
+                                                             v.ny, v.nz);
             MSF_LAUNCH_CHECK();
+            pc = pn;
         }
-        {   // s = Lambda A p  (transpose already in p->d_xT)
+        {   // s = Lambda A p  (pairs already built)
             const ProjDims& d = p->dims;
             dim3 block(p->fwd_bx, p->fwd_by);
             dim3 grid = fwd_grid(d, block);
             MSF_PROF("joseph_fwd", st);
-            joseph_fwd_kernel<FWD_LAMBDA><<<grid, block, 0, st>>>(dp->d_p, p->d_xT, p->d_col, dp->d_s, d_lambda, nullptr, d);
+            joseph_fwd_kernel<FWD_LAMBDA><<<grid, block, 0, st>>>(p->d_px, p->d_py, p->d_col, dp->d_s, d_lambda, nullptr, d);
             MSF_LAUNCH_CHECK();
         }
         // q = A^T s + p/sigma^2 ; alpha = rr / p.q
-        MSF_TRY(launch_adj(p, ADJ_CG_Q, dp->d_s, dp->d_q, dp->d_p, nullptr, nullptr, dp->d_partial, inv_s2, st));
+        MSF_TRY(launch_adj(p, ADJ_CG_Q, dp->d_s, dp->d_q, pc, nullptr, nullptr, dp->d_partial, inv_s2, st));
         {
             MSF_PROF("cg_finalize", st);
             cg_finalize_kernel<FIN_ALPHA><<<nt, 256, 0, st>>>(dp->d_partial, adj_parts(p), dp->d_rr, dp->d_alpha, dp->d_status);
@@ -873,7 +896,7 @@ extern "C" msf_status msf_prox_data(msf_dataprox* dp, const float* d_y, const fl
         }
         {   // z += alpha p ; r -= alpha q ; beta = r.r / rr
             MSF_PROF("cg_update", st);
-            cg_update_kernel<<<dim3(dp->parts_upd, nt), 256, 0, st>>>(d_x, dp->d_r, dp->d_p, dp->d_q, dp->d_alpha, dp->d_partial, fs);
+            cg_update_kernel<<<dim3(dp->parts_upd, nt), 256, 0, st>>>(d_x, dp->d_r, pc, dp->d_q, dp->d_alpha, dp->d_partial, fs);
             MSF_LAUNCH_CHECK();
         }
         {
@@ -1091,7 +1114,8 @@ extern "C" msf_status msf_projector_autotune(msf_projector* p, void* stream, int
         cudaEventElapsedTime(&ms, e0, e1);
         return ms;
     };
-    MSF_TRY_CUDA(cudaMemsetAsync(p->d_xT, 0, nv * sizeof(float), st));
+    MSF_TRY_CUDA(cudaMemsetAsync(p->d_px, 0, nv * sizeof(float2), st));
+    MSF_TRY_CUDA(cudaMemsetAsync(p->d_py, 0, nv * sizeof(float2), st));
     MSF_TRY_CUDA(cudaMemsetAsync(p->d_sw, 0, ns * sizeof(float), st));
     const int shapes[3][2] = {{32, 4}, {64, 2}, {16, 8}};
     float best = 1e30f;
@@ -1103,7 +1127,7 @@ extern "C" msf_status msf_projector_autotune(msf_projector* p, void* stream, int
             const ProjDims& d = p->dims;
             dim3 block(p->fwd_bx, p->fwd_by);
             dim3 grid = fwd_grid(d, block);
-            joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(p->d_xT, p->d_xT, p->d_col, tmp, nullptr, nullptr, d);
+            joseph_fwd_kernel<FWD_PLAIN><<<grid, block, 0, st>>>(p->d_px, p->d_py, p->d_col, tmp, nullptr, nullptr, d);
         });
         if (ms < best) { best = ms; bi = i; }
     }
