@@ -303,6 +303,10 @@ void msf_mace_destroy(msf_mace* m);
  * X_0 <- L~(W_0; X_0) (warm-started CG), X_k <- H_k(W_k); the average of Eq. (9)
  * uses mu.  h_residual (optional, synchronises) receives the FP64 consensus
  * spread sqrt(sum_i mu_i ||X_i - Xbar||^2) / ||Xbar|| of the new X.
+ * With the q-GGMRF prior the data agent and the prior agent run concurrently
+ * on two internal streams forked from `stream` and joined before the
+ * consensus (the CNN agents run in stream order); the step as a whole is
+ * ordered on `stream`.
  * With prm->use_graph the whole iteration (every kernel and the residual copy)
  * is captured once on an internal stream into a CUDA graph and replayed on
  * `stream`; the graph is re-captured when the parameters or the CNN's weights

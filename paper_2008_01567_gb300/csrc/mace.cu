@@ -5,9 +5,10 @@
 //   W <- W + 2 rho (Z - X)
 //
 // The consensus update is one pass over the K+1 stacked states that also forms
-// the FP64 partial sums of the consensus spread of X.  One iteration can be
-// captured once into a CUDA graph and replayed; a batch of independent
-// problems runs on forked streams inside one captured graph.
+// the FP64 partial sums of the consensus spread of X.  With the q-GGMRF prior
+// the data agent and the prior agent run concurrently on two forked streams.
+// One iteration can be captured once into a CUDA graph and replayed; a batch of
+// independent problems runs on forked streams inside one captured graph.
 #include <math.h>
 #include <string.h>
 
@@ -23,6 +24,10 @@ struct msf_mace {
     double* h_sums = nullptr;      // pinned [2], written by the step's last copy
     int nblocks = 0;
     size_t N = 0;                  // voxels of one 4D volume
+    // with the q-GGMRF prior the data agent and the prior agent run on two
+    // streams forked from the caller's and joined before the consensus
+    cudaStream_t s_prox = nullptr, s_prior = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_prox = nullptr, ev_prior = nullptr;
     // graph replay of one iteration
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -166,17 +171,36 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
     const size_t N = m->N;
     const int K1 = d.K + 1;
     const msf_vol* vol = projector_volume(d.proj);
-    void* sv = reinterpret_cast<void*>(st);
+    // The agents of F~ read disjoint blocks of W and write disjoint blocks of X.
+    // With the q-GGMRF prior the data agent runs on a low-priority stream beside
+    // the prior agent on a high-priority one, both joined before the consensus.
+    // The CNN agents stay in stream order: beside the data agent's projector
+    // kernels the persistent tcgen05 convs lose about a third of their speed
+    // (they share the L1 / shared-memory pipe and HBM), a net loss.
+    const bool fork = d.prior == MSF_PRIOR_QGGMRF;
+    if (fork) {
+        MSF_TRY_CUDA(cudaEventRecord(m->ev_fork, st));
+        MSF_TRY_CUDA(cudaStreamWaitEvent(m->s_prox, m->ev_fork, 0));
+        MSF_TRY_CUDA(cudaStreamWaitEvent(m->s_prior, m->ev_fork, 0));
+    }
+    void* sp = reinterpret_cast<void*>(fork ? m->s_prox : st);
+    void* sa = reinterpret_cast<void*>(fork ? m->s_prior : st);
     // X_0 <- L~(W_0; X_0)
-    MSF_TRY(msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, sv));
+    MSF_TRY(msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, sp));
     // X_k <- H_k(W_k)
     for (int k = 1; k < K1; ++k) {
         if (d.prior == MSF_PRIOR_QGGMRF) {
-            MSF_TRY(msf_prox_qggmrf(vol, &d.mrf, d.d_W + k * N, d.d_X + k * N, prm->sigma, prm->n_sweeps, sv));
+            MSF_TRY(msf_prox_qggmrf(vol, &d.mrf, d.d_W + k * N, d.d_X + k * N, prm->sigma, prm->n_sweeps, sa));
         } else {
             const msf_orient o = d.K == 1 ? d.orient : (msf_orient)(k - 1);
-            MSF_TRY(msf_denoise(d.cnn, o, vol, d.d_W + k * N, d.d_X + k * N, sv));
+            MSF_TRY(msf_denoise(d.cnn, o, vol, d.d_W + k * N, d.d_X + k * N, sa));
         }
+    }
+    if (fork) {
+        MSF_TRY_CUDA(cudaEventRecord(m->ev_prox, m->s_prox));
+        MSF_TRY_CUDA(cudaEventRecord(m->ev_prior, m->s_prior));
+        MSF_TRY_CUDA(cudaStreamWaitEvent(st, m->ev_prox, 0));
+        MSF_TRY_CUDA(cudaStreamWaitEvent(st, m->ev_prior, 0));
     }
     // Z <- G(2X - W);  W <- W + 2 rho (Z - X)
     MaceCoef c;
@@ -257,6 +281,18 @@ static msf_status enqueue_batch(msf_mace_batch* b, const msf_mace_params* prm, c
 
 using namespace msf;
 
+// The two agent streams (the prior agent at the highest priority, the data
+// agent at the lowest) and the fork/join events.
+static bool make_agent_streams(msf_mace* m) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return false;
+    return cudaStreamCreateWithPriority(&m->s_prior, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+           cudaStreamCreateWithPriority(&m->s_prox, cudaStreamNonBlocking, least) == cudaSuccess &&
+           cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&m->ev_prox, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&m->ev_prior, cudaEventDisableTiming) == cudaSuccess;
+}
+
 extern "C" msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out) {
     MSF_REQUIRE(desc && out, "msf_mace_create: NULL argument");
     *out = nullptr;
@@ -289,7 +325,8 @@ extern "C" msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out)
     if (cudaMalloc(&m->d_partial, 2 * m->nblocks * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->d_sums, 2 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&m->h_sums, 2 * sizeof(double)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        !make_agent_streams(m)) {
         cudaGetLastError();
         msf_mace_destroy(m);
         return fail(MSF_ERR_NOMEM, "msf_mace_create: out of memory");
@@ -302,6 +339,11 @@ extern "C" void msf_mace_destroy(msf_mace* m) {
     if (!m) return;
     drop_graph(m->gexec);
     if (m->cap) cudaStreamDestroy(m->cap);
+    if (m->s_prox) cudaStreamDestroy(m->s_prox);
+    if (m->s_prior) cudaStreamDestroy(m->s_prior);
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    if (m->ev_prox) cudaEventDestroy(m->ev_prox);
+    if (m->ev_prior) cudaEventDestroy(m->ev_prior);
     msf_dataprox_destroy(m->dp);
     cudaFree(m->d_partial);
     cudaFree(m->d_sums);
