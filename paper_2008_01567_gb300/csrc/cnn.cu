@@ -451,27 +451,35 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 // producer warps build each pixel's 45 inputs (5 frames x 3 x 3, padded to
 // K = 64, k = frame * 9 + ky * 3 + kx) as a 128-byte BF16 row in shared
 // memory; one MMA warp multiplies a 128-pixel tile by the packed 64 x 64
-// weights (four K16 steps); four epilogue warps store relu(acc + bias) as BF16
+// weights (four K16 steps); epilogue warps store relu(acc + bias) as BF16
 // activations.  A tile is 4 image rows x 32 columns; tile row q is accumulator
-// lanes 32q .. 32q + 31.
+// lanes 32q .. 32q + 31.  With four MMAs per tile the epilogue of a tile (TMEM
+// load, conversion, staging, store) is a long chain, so two groups of four
+// epilogue warps take alternate tiles; a warp of its own issues the patch
+// copies, so that no producer waits for the others before its next tile.
 constexpr int C1_ROWS = 4, C1_COLS = 32;
-constexpr int C1_THREADS = 288;   // warp 0 MMA, warps 1-4 producers, warps 5-8 epilogue
+constexpr int C1_EPI_GROUPS = 2;
+constexpr int C1_LOADER_WARP = 5;
+constexpr int C1_THREADS = 32 * (2 + 4 + 4 * C1_EPI_GROUPS);   // warp 0 MMA, 1-4 producers, 5 loader, then the epilogue
 
 constexpr int C1_PCOLS = C1_COLS + 8, C1_PROWS = C1_ROWS + 2;   // frame patch: 40 x 6 FP32
 
 struct C1Cfg {
     static constexpr int NS = 4;                              // A-operand stages
     static constexpr int NF = 4;                              // frame-patch stages
+    static constexpr int NB = 2 * C1_EPI_GROUPS;              // TMEM accumulators, 64 columns each
+    static constexpr int TMEM_ALLOC = 256;
     static constexpr int STAGE_BYTES = TILE_BYTES;            // 128 rows x 128 B
     static constexpr int PATCH_BYTES = C1_PCOLS * C1_PROWS * 4;   // 960 B copied per patch
     static constexpr int PATCH_STRIDE = 1024;                 // patches 128-byte aligned in shared memory
     static constexpr int F_BYTES = FRAMES * PATCH_STRIDE;     // one tile's five patches
     static constexpr int W_BYTES = CH * 128;
-    static constexpr int O_BYTES = TILE_BYTES;
+    static constexpr int O_BYTES = C1_EPI_GROUPS * TILE_BYTES;   // one staging tile per epilogue group
     static constexpr int BAR_BYTES = 512;
     static constexpr int SMEM = 1024 + NS * STAGE_BYTES + W_BYTES + O_BYTES + NF * F_BYTES + BAR_BYTES;
-    static_assert((2 * NS + 2 * NF + 5) * 8 + 8 <= 256, "barrier block overflows into the bias");
+    static_assert((2 * NS + 2 * NF + 2 * NB + 1) * 8 + 8 <= 256, "barrier block overflows into the bias");
     static_assert(F_BYTES % 128 == 0, "frame stages must stay 128-byte aligned");
+    static_assert(NB * CH <= TMEM_ALLOC, "accumulators exceed the TMEM allocation");
 };
 
 __device__ __forceinline__ void decode_c1_tile(const TileGeom& tg, int tile, int& img, int& a0, int& b0) {
@@ -503,8 +511,8 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
     uint64_t* ffull = bars + 2 * NS;
     uint64_t* fempty = ffull + NF;   // all 128 producers have read a patch stage
     uint64_t* tfull = fempty + NF;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* wbar = tempty + 2;
+    uint64_t* tempty = tfull + C::NB;
+    uint64_t* wbar = tempty + C::NB;
     uint32_t* tmem_slot = (uint32_t*)(wbar + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     float* sbias = (float*)((uint8_t*)bars + 256);
@@ -520,7 +528,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
             tc::mbar_init(&ffull[f], 1);
             tc::mbar_init(&fempty[f], 128);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::NB; ++b) {
             tc::mbar_init(&tfull[b], 1);
             tc::mbar_init(&tempty[b], 128);
         }
@@ -529,7 +537,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
         tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_alloc(tmem_slot, C::TMEM_ALLOC);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
@@ -553,7 +561,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
             const uint32_t w_base = tc::smem_u32(sW);
             int it = 0;
             for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x, ++it) {
-                const int s = it % NS, u = it / NS, ab = it & 1, ua = it >> 1;
+                const int s = it % NS, u = it / NS, ab = it % C::NB, ua = it / C::NB;
                 if (ua > 0 && !tc::mbar_wait(&tempty[ab], (ua - 1) & 1, abort_flag)) { ok = false; break; }
                 if (!tc::mbar_wait(&full[s], u & 1, abort_flag)) { ok = false; break; }
                 tc::fence_after_sync();
@@ -567,26 +575,43 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
             }
             if (!ok) give_up(MSF_ERR_TIMEOUT);
         }
-    } else if (warp <= 4) {
-        // ---------------- producers: warp 1 + r builds tile row r; thread 32
-        // (warp 1, lane 0) also issues the frame-patch copies NF tiles ahead
-        const int r = warp - 1;
-        const bool loader = PATCH && threadIdx.x == 32;
-        auto load_patches = [&](int tile, int fs) {
-            int img, a0, b0;
-            decode_c1_tile(tg, tile, img, a0, b0);
-            const int t = g.t0 + img / g.S, sl = img % g.S;
-            tc::mbar_expect_tx(&ffull[fs], FRAMES * C::PATCH_BYTES);
+    } else if (warp == C1_LOADER_WARP) {
+        // ---------------- frame-patch copies: tile it into patch stage it % NF,
+        // once all 128 producers are done with that stage's previous tile
+        if (PATCH && lane == 0) {
+            int issued[NF];
+            for (int f = 0; f < NF; ++f) issued[f] = 0;
+            bool ok = true;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
+                const int fs = it % NF, fu = it / NF;
+                if (fu > 0 && !tc::mbar_wait(&fempty[fs], (fu - 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                int img, a0, b0;
+                decode_c1_tile(tg, tile, img, a0, b0);
+                const int t = g.t0 + img / g.S, sl = img % g.S;
+                tc::fence_proxy_async_smem();
+                tc::mbar_expect_tx(&ffull[fs], FRAMES * C::PATCH_BYTES);
 #pragma unroll
-            for (int c = 0; c < FRAMES; ++c) {
-                const int tc_ = min(max(t + c - 2, 0), g.nt - 1);
-                tc::tma_load_4d(sF + fs * C::F_BYTES + c * C::PATCH_STRIDE, &map_f, &ffull[fs], b0 - 4, a0 - 1, sl,
-                                tc_ - pf.first);
+                for (int c = 0; c < FRAMES; ++c) {
+                    const int tc_ = min(max(t + c - 2, 0), g.nt - 1);
+                    tc::tma_load_4d(sF + fs * C::F_BYTES + c * C::PATCH_STRIDE, &map_f, &ffull[fs], b0 - 4, a0 - 1,
+                                    sl, tc_ - pf.first);
+                }
+                issued[fs] = fu + 1;
             }
-        };
-        if (loader)
-            for (int k = 0; k < NF && blockIdx.x + k * gridDim.x < tg.total; ++k)
-                load_patches(blockIdx.x + k * gridDim.x, k);
+            if (!ok) {
+                give_up(MSF_ERR_TIMEOUT);
+                // let the copies already issued land before the CTA exits
+                for (int f = 0; f < NF; ++f)
+                    if (issued[f] > 0) tc::mbar_wait(&ffull[f], (issued[f] - 1) & 1, nullptr, 100000000ull);
+            }
+        }
+    } else if (warp <= 4) {
+        // ---------------- producers: warp 1 + r builds tile row r
+        const int r = warp - 1;
         int it = 0;
         for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
             const int s = it % NS, u = it / NS, fs = it % NF, fu = it / NF;
@@ -595,14 +620,22 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
                 give_up(MSF_ERR_TIMEOUT);
                 break;
             }
-            float v[FRAMES * 9];
+            uint32_t w[32];
             if (PATCH) {
                 // pixel (a0 + r, b0 + lane): patch row r + ky, column lane + kx + 3
                 const float* patch = reinterpret_cast<const float*>(sF + fs * C::F_BYTES) + r * C1_PCOLS + lane + 3;
+                auto tap = [&](int k) {
+                    return k < FRAMES * 9
+                               ? patch[(k / 9) * (C::PATCH_STRIDE / 4) + ((k % 9) / 3) * C1_PCOLS + (k % 3)]
+                               : 0.0f;
+                };
 #pragma unroll
-                for (int k = 0; k < FRAMES * 9; ++k)
-                    v[k] = patch[(k / 9) * (C::PATCH_STRIDE / 4) + ((k % 9) / 3) * C1_PCOLS + (k % 3)];
+                for (int i = 0; i < 32; ++i) {
+                    __nv_bfloat162 hv = __floats2bfloat162_rn(tap(2 * i), tap(2 * i + 1));
+                    w[i] = *reinterpret_cast<uint32_t*>(&hv);
+                }
             } else {
+                float v[FRAMES * 9];
                 int img, a0, b0;
                 decode_c1_tile(tg, tile, img, a0, b0);
                 const int a = a0 + r, b = b0 + lane;
@@ -623,14 +656,13 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
                                     v[c * 9 + ky * 3 + kx] = __ldg(f + (ky - 1) * g.W + (kx - 1));
                     }
                 }
-            }
-            uint32_t w[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const float lo = 2 * i < FRAMES * 9 ? v[2 * i] : 0.0f;
-                const float hi = 2 * i + 1 < FRAMES * 9 ? v[2 * i + 1] : 0.0f;
-                __nv_bfloat162 hv = __floats2bfloat162_rn(lo, hi);
-                w[i] = *reinterpret_cast<uint32_t*>(&hv);
+                for (int i = 0; i < 32; ++i) {
+                    const float lo = 2 * i < FRAMES * 9 ? v[2 * i] : 0.0f;
+                    const float hi = 2 * i + 1 < FRAMES * 9 ? v[2 * i + 1] : 0.0f;
+                    __nv_bfloat162 hv = __floats2bfloat162_rn(lo, hi);
+                    w[i] = *reinterpret_cast<uint32_t*>(&hv);
+                }
             }
             const int m = r * 32 + lane;     // accumulator row of this pixel
             uint8_t* row = sA + s * C::STAGE_BYTES + m * 128;
@@ -640,25 +672,16 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
                     make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&full[s]);
-            if (PATCH) {
-                // once every producer is done with patch stage fs, refill it NF tiles ahead
-                tc::mbar_arrive(&fempty[fs]);
-                if (loader && tile + NF * (int)gridDim.x < tg.total) {
-                    if (!tc::mbar_wait(&fempty[fs], fu & 1, abort_flag)) {
-                        give_up(MSF_ERR_TIMEOUT);
-                        break;
-                    }
-                    tc::fence_proxy_async_smem();
-                    load_patches(tile + NF * gridDim.x, fs);
-                }
-            }
+            if (PATCH) tc::mbar_arrive(&fempty[fs]);   // this producer is done with patch stage fs
         }
     } else {
-        // ---------------- epilogue: warp 5 + i, TMEM lane quarter q = warp % 4 = tile row q
-        const int q = warp & 3;
-        int it = 0;
-        for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
-            const int ab = it & 1, ua = it >> 1;
+        // ---------------- epilogue: group e = (warp - 6) / 4 takes tiles
+        // it = e, e + C1_EPI_GROUPS, ...; TMEM lane quarter q = warp % 4 = tile row q
+        const int q = warp & 3, grp = (warp - C1_LOADER_WARP - 1) / 4;
+        int it = grp;
+        for (int tile = blockIdx.x + grp * gridDim.x; tile < tg.total;
+             tile += C1_EPI_GROUPS * gridDim.x, it += C1_EPI_GROUPS) {
+            const int ab = it % C::NB, ua = it / C::NB;
             if (!tc::mbar_wait(&tfull[ab], ua & 1, abort_flag)) {
                 give_up(MSF_ERR_TIMEOUT);
                 break;
@@ -685,7 +708,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
                 w[2 * k] = *reinterpret_cast<uint32_t*>(&h0);
                 w[2 * k + 1] = *reinterpret_cast<uint32_t*>(&h1);
             }
-            uint8_t* stage = sO + q * (TILE_BYTES / 4);
+            uint8_t* stage = sO + grp * TILE_BYTES + q * (TILE_BYTES / 4);
             if (lane == 0) tc::tma_store_wait_read<0>();
             __syncwarp();
 #pragma unroll
@@ -705,7 +728,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tmem_base, TMEM_COLS);
+        tc::tmem_dealloc(tmem_base, C::TMEM_ALLOC);
     }
 }
 
