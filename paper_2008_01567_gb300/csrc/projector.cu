@@ -5,7 +5,7 @@
 // cone-beam reference; the geometry is documented in msf.h).  The adjoint is a
 // voxel-driven gather: each voxel enumerates the rays whose bilinear footprint
 // touches it and recomputes the forward's interpolation coordinates with the
-// same FP32 operations (the z crossing to within a few 1e-6 voxel): A^T is the
+// same FP32 operations (the z crossing to within a few 1e-5 voxel): A^T is the
 // transpose of the FP32 A up to rounding, without atomics.
 //
 // Per (view, detector column) constants are computed once in FP64 and stored
@@ -333,10 +333,11 @@ __device__ __forceinline__ float u_pixel(float x, float y, float cs, float sn, c
 // the segment {x = x_ix, |y - y_iy| <= voxel} (plus one column of margin); on
 // a column that qualifies, the rows whose f_z(k) can fall within one voxel of
 // the run follow from f_z(v) = c_z + v (c1 + tk inv_dmaj).  Each ray's f_a is
-// recomputed with the forward's own operations (bit for bit); f_z of the
-// column's first candidate row likewise, and of the next rows by one FMA along
-// the row (a few 1e-6 voxel from the forward's value, so the taps agree except
-// within that distance of a voxel boundary, where the weights are continuous).
+// recomputed with the forward's own operations (bit for bit); f_z of row 0
+// likewise, and of a row iv by one FMA from it (a few 1e-5 voxel from the
+// forward's value, so the taps agree except within that distance of a voxel
+// boundary, where the weights are continuous; the value depends on the ray
+// alone, not on the run length the plan's autotuner picks).
 // Every ray-plane crossing of the forward is visited by the two runs that hold
 // its a-taps, so the work tracks the forward's.
 template <bool XMAJ, int ZB>
@@ -376,21 +377,40 @@ __device__ __forceinline__ void gather_runs(const float4* __restrict__ col, cons
         const int iv_lo = max(0, (int)floorf(va) - 1);
         const int iv_hi = min(d.nv - 1, (int)ceilf(vb) + 1);
         const float* erow = e + ((size_t)g * d.nv) * d.nu + iu;
-        // f_z is affine in the row: the first row's crossing with the forward's
-        // operations, the others one FMA away from it (within a few 1e-6 voxel)
-        const RayZ rz0 = ray_z(c, det_v(iv_lo, d), d.cz);
-        const float fz0 = __fmaf_rn(tk, rz0.bz, rz0.fz_mid);
-        const float dfz = d.dv * __fmaf_rn(tk, c.inv_dmaj, c.c1);
-        for (int iv = iv_lo; iv <= iv_hi; ++iv) {
-            const float fz = __fmaf_rn((float)(iv - iv_lo), dfz, fz0);
+        // f_z is affine in the row: f_z(iv) = f_z(0) + iv dfz, with f_z(0) the
+        // forward's crossing of detector row 0 (so a ray's value does not
+        // depend on the run that evaluates it; within a few 1e-5 voxel of the
+        // forward's own FP32 value)
+        const RayZ rzb = ray_z(c, det_v(0, d), d.cz);
+        const float fzb = __fmaf_rn(tk, rzb.bz, rzb.fz_mid);
+        const float dfz = d.dv * __fmaf_rn(tk, c.inv_dmaj, c.c1);   // > 0
+        // rows in [iva, ivb) have both z taps inside the run (f_z in
+        // [iz_lo + 0.01, iz_lo + ZB - 1.01]); the others are checked
+        const float rdfz = __fdividef(1.0f, dfz);
+        const int iva = min(max((int)ceilf(((float)iz_lo + 0.01f - fzb) * rdfz), iv_lo), iv_hi + 1);
+        const int ivb = min(max((int)floorf(((float)(iz_lo + ZB) - 1.01f - fzb) * rdfz) + 1, iva), iv_hi + 1);
+        // explicit roundings: both loops must form a row's terms identically
+        auto checked = [&](int iv) {
+            const float fz = __fmaf_rn((float)iv, dfz, fzb);
             const float z0f = floorf(fz);
             const int k0 = (int)z0f - iz_lo;
-            if (k0 < -1 || k0 >= ZB) continue;
-            const float wz1 = __fsub_rn(fz, z0f);
-            const float ev = wa * __ldg(erow + (size_t)iv * d.nu);
-            if (k0 >= 0) acc[k0][tid] += __fsub_rn(1.0f, wz1) * ev;
-            if (k0 + 1 < ZB) acc[k0 + 1][tid] += wz1 * ev;
+            if (k0 < -1 || k0 >= ZB) return;
+            const float ev = __fmul_rn(wa, __ldg(erow + (size_t)iv * d.nu));
+            const float c1 = __fmul_rn(__fsub_rn(fz, z0f), ev);
+            if (k0 >= 0) acc[k0][tid] = __fadd_rn(acc[k0][tid], __fsub_rn(ev, c1));
+            if (k0 + 1 < ZB) acc[k0 + 1][tid] = __fadd_rn(acc[k0 + 1][tid], c1);
+        };
+        for (int iv = iv_lo; iv < iva; ++iv) checked(iv);
+        for (int iv = iva; iv < ivb; ++iv) {
+            const float fz = __fmaf_rn((float)iv, dfz, fzb);
+            const float z0f = floorf(fz);
+            const int k0 = min(max((int)z0f - iz_lo, 0), ZB - 2);   // in range by the choice of [iva, ivb)
+            const float ev = __fmul_rn(wa, __ldg(erow + (size_t)iv * d.nu));
+            const float c1 = __fmul_rn(__fsub_rn(fz, z0f), ev);
+            acc[k0][tid] = __fadd_rn(acc[k0][tid], __fsub_rn(ev, c1));
+            acc[k0 + 1][tid] = __fadd_rn(acc[k0 + 1][tid], c1);
         }
+        for (int iv = ivb; iv <= iv_hi; ++iv) checked(iv);
     }
 }
 
@@ -399,8 +419,9 @@ __device__ __forceinline__ void gather_runs(const float4* __restrict__ col, cons
 //   ADJ_PLAIN:   out = A^T e
 //   ADJ_CG_INIT: r = A^T e + (v - z)/sigma^2, p = r, partial sum r.r
 //   ADJ_CG_Q:    q = A^T e + p/sigma^2, partial sum p.q
+// (at most 64 registers: eight blocks per SM, no spills)
 template <int MODE, int ZB>
-__global__ void __launch_bounds__(128) joseph_adj_kernel(
+__global__ void __launch_bounds__(128, 8) joseph_adj_kernel(
     const float4* __restrict__ col, const float2* __restrict__ trig, const int* __restrict__ vflag,
     const float* __restrict__ e, float* __restrict__ out, const float* __restrict__ a1,
     const float* __restrict__ a2, float* __restrict__ out2, double* __restrict__ partial,
