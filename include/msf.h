@@ -116,6 +116,13 @@ size_t msf_projector_bytes(const msf_projector* p);
  * h_choice (optional, 3 ints) receives {block columns, block rows, z-run}. */
 msf_status msf_projector_autotune(msf_projector* p, void* stream, int* h_choice);
 
+/* Sets the same two launch shapes directly (no paper counterpart: a launch
+ * parameter, for callers that want a fixed configuration, e.g. to reproduce
+ * a tuned run without timing it again).  fwd_cols x fwd_rows must be 32x4,
+ * 64x2 or 16x8 and adj_zrun 8, 16 or 32; anything else is MSF_ERR_ARG and
+ * leaves the plan unchanged.  Results do not depend on the choice. */
+msf_status msf_projector_set_tuning(msf_projector* p, int fwd_cols, int fwd_rows, int adj_zrun);
+
 /* y = A x for every time-point: the system matrix A_n of Sec. II, Eq. (2),
  * modelled as a Joseph ray-driven projector.  For each ray (one per detector
  * pixel and view) the major axis is x when |d_x| >= |d_y| else y; on every

@@ -1113,6 +1113,19 @@ extern "C" msf_status msf_project_static(const msf_geom* geom, const msf_vol* vo
 
 // ====================================================================== autotuning
 
+extern "C" msf_status msf_projector_set_tuning(msf_projector* p, int fwd_cols, int fwd_rows, int adj_zrun) {
+    MSF_REQUIRE(p, "msf_projector_set_tuning: NULL plan");
+    MSF_REQUIRE((fwd_cols == 32 && fwd_rows == 4) || (fwd_cols == 64 && fwd_rows == 2) ||
+                    (fwd_cols == 16 && fwd_rows == 8),
+                "msf_projector_set_tuning: forward block %dx%d is not 32x4, 64x2 or 16x8", fwd_cols, fwd_rows);
+    MSF_REQUIRE(adj_zrun == 8 || adj_zrun == 16 || adj_zrun == 32,
+                "msf_projector_set_tuning: adjoint z-run %d is not 8, 16 or 32", adj_zrun);
+    p->fwd_bx = fwd_cols;
+    p->fwd_by = fwd_rows;
+    p->adj_zb = adj_zrun;
+    return MSF_OK;
+}
+
 extern "C" msf_status msf_projector_autotune(msf_projector* p, void* stream, int* h_choice) {
     MSF_REQUIRE(p, "msf_projector_autotune: NULL plan");
     cudaStream_t st = as_stream(stream);

@@ -93,6 +93,7 @@ _SIGS = {
     "msf_mace_batch_destroy": (None, [_P]),
     "msf_mace_batch_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
     "msf_projector_autotune": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "msf_projector_set_tuning": (_I, [_P, _I, _I, _I]),
     "msf_selftest_wait": (_I, [ctypes.c_uint64, _P]),
     "msf_phantom_voxelize": (_I, [ctypes.POINTER(msf_vol), _P, _I, _I, _P, _P]),
     "msf_phantom_project": (_I, [_P, _P, _I, _P, _P]),
@@ -403,6 +404,10 @@ def msf_projector_autotune(proj: Projector, stream=None):
     choice = (ctypes.c_int * 3)()
     _check(lib().msf_projector_autotune(proj.handle, _stream(stream), choice))
     return tuple(choice)
+
+
+def msf_projector_set_tuning(proj: Projector, fwd_cols: int, fwd_rows: int, adj_zrun: int):
+    _check(lib().msf_projector_set_tuning(proj.handle, fwd_cols, fwd_rows, adj_zrun))
 
 
 # ------------------------------------------------------------------ phantoms

@@ -53,6 +53,7 @@ def test_argument_errors_before_launch(lib):
     assert lib.msf_prox_qggmrf(ctypes.byref(vol), ctypes.byref(mrf), 1, 1, 0.1, 1, None) == 1
     assert b"p == 2" in lib.msf_last_error()
     assert lib.msf_weights(1, 1, 1, 10, -1.0, 1.0, None) == 1
+    assert lib.msf_projector_set_tuning(None, 32, 4, 16) == 1
     assert lib.msf_version().startswith(b"msf-gb300")
 
 

@@ -115,3 +115,32 @@ def test_autotune_keeps_results(M):
     M.msf_backproject(P, e, b1)
     torch.cuda.synchronize()
     assert torch.equal(y0, y1) and torch.equal(b0, b1)
+
+
+def test_every_launch_shape_gives_the_same_results(M):
+    # the forward's ray blocks and the adjoint's z-run lengths only reorganise
+    # the launch: each ray keeps its arithmetic and each voxel its summation
+    # order, so all nine configurations agree bit for bit (a ragged volume, so
+    # that runs and blocks end inside the grid)
+    import torch
+    scan = synth.Scan(n=44, nt=3, nu=61, nv=47, views=7)
+    P = M.Projector(scan)
+    x = torch.empty((scan.nt, scan.n, scan.n, scan.n), device="cuda")
+    M.msf_phantom_voxelize(P.vol, synth.ellipsoids(98, 4, scan), x, ss=1)
+    e = torch.rand((scan.nt, scan.views, scan.nv, scan.nu), device="cuda",
+                   generator=torch.Generator("cuda").manual_seed(2))
+    ref_y = ref_b = None
+    for cols, rows in ((32, 4), (64, 2), (16, 8)):
+        for zrun in (8, 16, 32):
+            M.msf_projector_set_tuning(P, cols, rows, zrun)
+            y, b = torch.empty_like(e), torch.empty_like(x)
+            M.msf_project(P, x, y)
+            M.msf_backproject(P, e, b)
+            torch.cuda.synchronize()
+            if ref_y is None:
+                ref_y, ref_b = y, b
+            assert torch.equal(y, ref_y) and torch.equal(b, ref_b), (cols, rows, zrun)
+    with pytest.raises(M.MsfError):
+        M.msf_projector_set_tuning(P, 128, 1, 16)
+    with pytest.raises(M.MsfError):
+        M.msf_projector_set_tuning(P, 32, 4, 12)
