@@ -740,9 +740,9 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
 // (a0 + 2i + 1, b0 + j) in columns 64-127 (group 1).  Input row a0 + 2i + s,
 // s = -1 .. 2, reaches group 0 through kernel row dy = s and group 1 through
 // dy = s - 1, so one A slice feeds both groups with B = [W(dy = s); W(dy = s-1)]
-// (N = 128; N = 64 at s = -1 and s = 2 where one group has no tap).  A
-// tcgen05.mma costs about as much at N = 64 as at N = 128 on this part, so the
-// 12 A slices x 4 K-steps per 256 pixels replace 18 x 4 of the 16 x 8 tile.
+// (N = 128; N = 64 at s = -1 and s = 2 where one group has no tap).  The
+// tensor math is the same as in the 16 x 8 tile, issued as 12 A slices x 4
+// K-steps per 256 pixels instead of 18 x 4: fewer MMAs and A-slice reads.
 // Rows of one parity come from one TMA box: the activation maps view the
 // image rows as (H / 2 pairs) x (2 parities), which needs an even H.
 constexpr int PAIR_ROWS = 16;                                 // row pairs per tile
