@@ -205,3 +205,25 @@ def test_mace_fixed_point_is_map_solution(oracle):
     np.testing.assert_allclose(xhat.ravel(), exact, rtol=1e-7, atol=1e-9 * np.abs(exact).max())
     np.testing.assert_allclose(oracle.average(X, mu).ravel(), exact, rtol=1e-7, atol=1e-9 * np.abs(exact).max())
     assert res[-1] < 1e-7 < res[0]
+
+
+def test_consensus_residual_closed_forms(oracle):
+    # Sec. III stopping quantity r = sqrt(sum_i mu_i ||X_i - Xbar||^2) / ||Xbar||.
+    # Two agents, equal weights, constant fields a and b: Xbar = (a + b) / 2 and
+    # each deviation is |a - b| / 2, so r = |a - b| / |a + b|.
+    shape = (2, 3, 4, 5)
+    a, b = 1.25, 0.5
+    r = oracle.consensus_residual([np.full(shape, a), np.full(shape, b)], [0.5, 0.5])
+    assert r == pytest.approx(abs(a - b) / abs(a + b), rel=1e-14)
+    # agreeing agents: zero up to the rounding of Xbar; the residual does not
+    # change with the overall scale
+    x = synth.uniform(91, shape, 0.5, 1.5)
+    assert oracle.consensus_residual([x, x, x], [0.2, 0.3, 0.5]) <= 1e-15
+    y = synth.uniform(92, shape, 0.5, 1.5)
+    mu = [0.25, 0.75]
+    r1 = oracle.consensus_residual([x, y], mu)
+    assert oracle.consensus_residual([7.0 * x, 7.0 * y], mu) == pytest.approx(r1, rel=1e-13)
+    # unequal weights, worked by hand on scalars 1 and 0 with mu = (1/4, 3/4):
+    # Xbar = 1/4, deviations 3/4 and 1/4, r = sqrt(1/4 * 9/16 + 3/4 * 1/16) / (1/4) = sqrt(3)
+    r2 = oracle.consensus_residual([np.ones(1), np.zeros(1)], mu)
+    assert r2 == pytest.approx(math.sqrt(3.0), rel=1e-14)
