@@ -320,6 +320,24 @@ void msf_mace_destroy(msf_mace* m);
  * change.  Results are identical to the eager path. */
 msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, double* h_residual, void* stream);
 
+/* The consensus and Mann update of Algorithm 1 alone (Sec. III, Eqs. (8), (9),
+ * (12)): W_i <- W_i + 2 rho (sum_j mu_j (2 X_j - W_j) - X_i) on caller-owned
+ * stacks d_W, d_X of K1 = K + 1 states of N voxels each ([K1][N], FP32, K1 = 2
+ * or 4), for callers that run the agents themselves -- e.g. one problem split
+ * by time-point over ranks, each rank passing its own frames.  Also forms the
+ * two FP64 sums of the consensus spread over these voxels,
+ * d_work[MSF_CONSENSUS_SUMS] = sum_i mu_i ||X_i - Xbar||^2 and
+ * d_work[MSF_CONSENSUS_SUMS + 1] = ||Xbar||^2 (device memory; the spread of
+ * msf_mace_step is sqrt(first / second), with sums over all ranks when split).
+ * d_work: device workspace of MSF_CONSENSUS_WORK doubles, owned by the caller.
+ * Same kernels as msf_mace_step's consensus.  Errors: MSF_ERR_ARG for NULL
+ * pointers, another K1, N = 0, rho outside (0,1), negative weights or weights
+ * not summing to 1, before any launch. */
+#define MSF_CONSENSUS_SUMS 2432
+#define MSF_CONSENSUS_WORK 2434
+msf_status msf_mace_consensus(float* d_W, const float* d_X, int K1, size_t N, const double* mu, double rho,
+                              double* d_work, void* stream);
+
 /* A queue of independent (uneven) MACE problems advanced together: each
  * problem runs on its own internal stream forked from the caller's stream and
  * joined back, so small problems share the GPU; with use_graph set for every

@@ -150,6 +150,35 @@ __global__ void sum2_kernel(const double* __restrict__ partial, int n, double* _
     }
 }
 
+constexpr int CONSENSUS_BLOCKS = 152 * 8;
+static_assert(MSF_CONSENSUS_SUMS == 2 * CONSENSUS_BLOCKS && MSF_CONSENSUS_WORK == MSF_CONSENSUS_SUMS + 2,
+              "msf_mace_consensus workspace layout");
+
+// The consensus pass over K1 stacked states of N voxels each, then the two
+// FP64 sums (into sums[0..1]) of the per-block partials.
+static msf_status launch_consensus(float* W, const float* X, int K1, size_t N, const MaceCoef& c, double* partial,
+                                   double* sums, cudaStream_t st) {
+    {
+        MSF_PROF("mace_consensus", st);
+        const bool vec = N % 4 == 0 && (uintptr_t)W % 16 == 0 && (uintptr_t)X % 16 == 0;
+        if (K1 == 2 && vec)
+            consensus_kernel<2, true><<<CONSENSUS_BLOCKS, 256, 0, st>>>(W, X, N, c, partial);
+        else if (K1 == 2)
+            consensus_kernel<2, false><<<CONSENSUS_BLOCKS, 256, 0, st>>>(W, X, N, c, partial);
+        else if (vec)
+            consensus_kernel<4, true><<<CONSENSUS_BLOCKS, 256, 0, st>>>(W, X, N, c, partial);
+        else
+            consensus_kernel<4, false><<<CONSENSUS_BLOCKS, 256, 0, st>>>(W, X, N, c, partial);
+        MSF_LAUNCH_CHECK();
+    }
+    {
+        MSF_PROF("mace_residual", st);
+        sum2_kernel<<<1, 1024, 0, st>>>(partial, CONSENSUS_BLOCKS, sums);
+        MSF_LAUNCH_CHECK();
+    }
+    return MSF_OK;
+}
+
 static msf_status check_params(const msf_mace* m, const msf_mace_params* prm) {
     MSF_REQUIRE(prm->rho > 0 && prm->rho < 1, "msf_mace_step: rho must lie in (0,1) (Eq. (12))");
     MSF_REQUIRE(prm->sigma > 0, "msf_mace_step: sigma must be positive");
@@ -207,24 +236,7 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
     for (int i = 0; i < 4; ++i) c.mu[i] = i < K1 ? (float)prm->mu[i] : 0.0f;
     c.two_rho = (float)(2.0 * prm->rho);
     c.K1 = K1;
-    {
-        MSF_PROF("mace_consensus", st);
-        const bool vec = N % 4 == 0 && (uintptr_t)d.d_W % 16 == 0 && (uintptr_t)d.d_X % 16 == 0;
-        if (K1 == 2 && vec)
-            consensus_kernel<2, true><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
-        else if (K1 == 2)
-            consensus_kernel<2, false><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
-        else if (vec)
-            consensus_kernel<4, true><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
-        else
-            consensus_kernel<4, false><<<m->nblocks, 256, 0, st>>>(d.d_W, d.d_X, N, c, m->d_partial);
-        MSF_LAUNCH_CHECK();
-    }
-    {
-        MSF_PROF("mace_residual", st);
-        sum2_kernel<<<1, 1024, 0, st>>>(m->d_partial, m->nblocks, m->d_sums);
-        MSF_LAUNCH_CHECK();
-    }
+    MSF_TRY(launch_consensus(d.d_W, d.d_X, K1, N, c, m->d_partial, m->d_sums, st));
     MSF_TRY_CUDA(cudaMemcpyAsync(m->h_sums, m->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     return MSF_OK;
 }
@@ -321,7 +333,7 @@ extern "C" msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out)
     // the projector's volume describes the problem
     const msf_vol* v = projector_volume(desc->proj);
     m->N = (size_t)v->nx * v->ny * v->nz * v->nt;
-    m->nblocks = 152 * 8;
+    m->nblocks = CONSENSUS_BLOCKS;
     if (cudaMalloc(&m->d_partial, 2 * m->nblocks * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->d_sums, 2 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&m->h_sums, 2 * sizeof(double)) != cudaSuccess ||
@@ -449,4 +461,24 @@ extern "C" msf_status msf_mace_batch_step(msf_mace_batch* b, const msf_mace_para
         for (int i = 0; i < n; ++i) MSF_TRY(read_residual(b->items[i], &h_residuals[i]));
     }
     return MSF_OK;
+}
+
+extern "C" msf_status msf_mace_consensus(float* d_W, const float* d_X, int K1, size_t N, const double* mu, double rho,
+                                         double* d_work, void* stream) {
+    MSF_REQUIRE(d_W && d_X && mu && d_work, "msf_mace_consensus: NULL argument");
+    MSF_REQUIRE(K1 == 2 || K1 == 4, "msf_mace_consensus: K + 1 must be 2 or 4, got %d", K1);
+    MSF_REQUIRE(N > 0, "msf_mace_consensus: empty states");
+    MSF_REQUIRE(rho > 0 && rho < 1, "msf_mace_consensus: rho must lie in (0,1) (Eq. (12))");
+    double musum = 0.0;
+    for (int i = 0; i < K1; ++i) {
+        MSF_REQUIRE(mu[i] >= 0, "msf_mace_consensus: agent weights must be non-negative");
+        musum += mu[i];
+    }
+    MSF_REQUIRE(fabs(musum - 1.0) < 1e-9, "msf_mace_consensus: agent weights must sum to 1 (got %.17g)", musum);
+    MSF_TRY(check_device());
+    MaceCoef c;
+    for (int i = 0; i < 4; ++i) c.mu[i] = i < K1 ? (float)mu[i] : 0.0f;
+    c.two_rho = (float)(2.0 * rho);
+    c.K1 = K1;
+    return launch_consensus(d_W, d_X, K1, N, c, d_work, d_work + 2 * CONSENSUS_BLOCKS, as_stream(stream));
 }

@@ -20,6 +20,7 @@ STATUS = {0: "MSF_OK", 1: "MSF_ERR_ARG", 2: "MSF_ERR_CUDA", 3: "MSF_ERR_NOMEM", 
           5: "MSF_ERR_NUMERIC", 6: "MSF_ERR_UNSUPPORTED"}
 MSF_XY_T, MSF_YZ_T, MSF_ZX_T = 0, 1, 2
 MSF_PRIOR_QGGMRF, MSF_PRIOR_CNN = 0, 1
+MSF_CONSENSUS_SUMS, MSF_CONSENSUS_WORK = 2432, 2434
 
 
 class MsfError(RuntimeError):
@@ -94,6 +95,7 @@ _SIGS = {
     "msf_mace_batch_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
     "msf_projector_autotune": (_I, [_P, _P, ctypes.POINTER(_I)]),
     "msf_projector_set_tuning": (_I, [_P, _I, _I, _I]),
+    "msf_mace_consensus": (_I, [_P, _P, _I, _Z, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _P, _P]),
     "msf_selftest_wait": (_I, [ctypes.c_uint64, _P]),
     "msf_phantom_voxelize": (_I, [ctypes.POINTER(msf_vol), _P, _I, _I, _P, _P]),
     "msf_phantom_project": (_I, [_P, _P, _I, _P, _P]),
@@ -372,6 +374,20 @@ def msf_mace_step(m: Mace, rho: float, sigma: float, mu, n_cg: int, n_sweeps: in
     _check(lib().msf_mace_step(m.handle, ctypes.byref(prm), ctypes.byref(r) if want_residual else None,
                                _stream(stream)))
     return r.value if want_residual else None
+
+
+def msf_mace_consensus(W, X, mu, rho: float, work, stream=None):
+    """Consensus and Mann update of stacked states W, X [K1, ...] in place; the
+    two FP64 sums of the consensus spread stay in work[MSF_CONSENSUS_SUMS:+2]
+    (work: CUDA float64 tensor of MSF_CONSENSUS_WORK elements)."""
+    import torch
+    K1 = W.shape[0]
+    if X.shape != W.shape:
+        raise ValueError("W and X must have the same shape")
+    if work.dtype != torch.float64 or work.numel() < MSF_CONSENSUS_WORK:
+        raise ValueError(f"work must be a float64 tensor of at least {MSF_CONSENSUS_WORK} elements")
+    m = (ctypes.c_double * 4)(*(list(mu) + [0.0] * (4 - len(mu))))
+    _check(lib().msf_mace_consensus(_f32(W), _f32(X), K1, W[0].numel(), m, rho, _ptr(work), _stream(stream)))
 
 
 class MaceBatch:

@@ -54,6 +54,11 @@ def test_argument_errors_before_launch(lib):
     assert b"p == 2" in lib.msf_last_error()
     assert lib.msf_weights(1, 1, 1, 10, -1.0, 1.0, None) == 1
     assert lib.msf_projector_set_tuning(None, 32, 4, 16) == 1
+    assert lib.msf_mace_consensus(None, None, 2, 8, None, 0.5, None, None) == 1
+    mu = (ctypes.c_double * 4)(0.5, 0.25, 0.25, 0.0)
+    fake = ctypes.c_void_p(256)                    # never dereferenced: the checks come first
+    assert lib.msf_mace_consensus(fake, fake, 3, 8, mu, 0.5, fake, None) == 1
+    assert b"2 or 4" in lib.msf_last_error()
     assert lib.msf_version().startswith(b"msf-gb300")
 
 
