@@ -32,9 +32,13 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def test_plain_mace_matches_oracle(M):
+@pytest.mark.parametrize("mode", ["sparse360", "wedge90"])
+def test_plain_mace_matches_oracle(M, mode):
+    # sparse-view (views interlaced over 360 deg) and limited-angle (each
+    # time-point a 90-deg wedge of a continuous rotation) scans of Sec. VI
+    import dataclasses
     import torch
-    scan = synth.TINY
+    scan = dataclasses.replace(synth.TINY, mode=mode)
     x0, counts, y, lam = measurement(scan, 41)
     sigma, rho, n_cg, iters = 0.1, 0.5, 5, 10
     mu = [0.5, 0.5]
