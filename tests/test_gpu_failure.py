@@ -1,7 +1,7 @@
 """Failure detection without a GPU fault: a device-side wait that nothing
 satisfies gives up after its limit and reports MSF_ERR_TIMEOUT; the context
-stays usable.  Argument and numerical errors are reported before or after
-launches without touching the device state."""
+stays usable.  Argument, numerical and out-of-memory errors are reported
+before or after launches without touching the device state."""
 import time
 
 import numpy as np
@@ -56,6 +56,29 @@ def test_nonfinite_input_is_reported(M):
     X2 = torch.zeros_like(W)
     m2 = M.Mace(P, W2, X2, y, y, M.MSF_PRIOR_QGGMRF, mrf=M.msf_mrf(2.0, 1.2, 1.0, 0.1, 0.5))
     assert np.isfinite(M.msf_mace_step(m2, 0.5, 0.1, [0.5, 0.5], 1, 1))
+
+
+def test_out_of_memory_is_reported_and_recoverable(M):
+    # allocations far beyond the device (2 x 128 TB of activations, ~4 PB of
+    # training workspace) fail in cudaMalloc and come back as MSF_ERR_NOMEM;
+    # the partial allocations are released and the context keeps working
+    import torch
+    with pytest.raises(M.MsfError) as e:
+        M.Cnn(1 << 40)
+    assert e.value.status == 3                 # MSF_ERR_NOMEM
+    c = M.Cnn(4096)
+    with pytest.raises(M.MsfError) as e:
+        c.train_reserve(1 << 40)
+    assert e.value.status == 3
+    c.train_reserve(1 << 12)
+    convs, bns = synth.cnn_weights(3)
+    c.set_params(M.pack_params(convs, bns))
+    shape = (2, 4, 8, 8)
+    x = torch.rand(shape, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    out = torch.empty_like(x)
+    M.msf_denoise(c, 0, M.msf_vol(8, 8, 4, 2, 1.0), x, out)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
 
 
 def test_checkpoint_resume_is_bit_identical(M):
