@@ -83,6 +83,12 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
         out, _ = self.p.communicate(timeout=10)
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out: str) -> dict:
+        """Median SM clock, maximum SM clock and the throttle reasons seen
+        active in nvidia-smi's CSV samples (noheader, nounits)."""
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
