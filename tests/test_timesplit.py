@@ -1,5 +1,5 @@
 """One problem split by time-point over ranks (paper_2008_01567_gb300.timesplit):
-the partition and halo arithmetic, and two gloo ranks on CPU running Algorithm 1
+the partition and halo arithmetic, and two or three gloo ranks on CPU running Algorithm 1
 with the FP64 oracle's agents on their own frames, against the oracle's MACE on
 the whole problem.  Every per-frame computation is the same on both sides, so
 the states agree to rounding (1e-12 relative)."""
@@ -11,7 +11,7 @@ import pytest
 
 from paper_2008_01567_gb300 import timesplit
 
-SCAN = dict(n=8, nt=5, nu=10, nv=9, views=4, mode="sparse360")   # 5 frames over 2 ranks: blocks of 3 and 2
+SCAN = dict(n=8, nt=5, nu=10, nv=9, views=4, mode="sparse360")
 SIGMA, RHO, N_CG, ITERS = 0.2, 0.8, 3, 3
 MU = [0.25, 0.25, 0.25, 0.25]
 ORIENTS = ("xy", "yz", "zx")
@@ -40,11 +40,11 @@ def test_halo_widths_at_the_ends():
     assert timesplit.halo_widths(0, 16, 16) == (0, 0)
 
 
-def _problem():
+def _problem(nt):
     import oracle
     from paper_2008_01567_gb300 import synth
     from tests._problems import measurement
-    scan = synth.Scan(**SCAN)
+    scan = synth.Scan(**dict(SCAN, nt=nt))
     _, _, y, lam = measurement(scan, 97)
     convs, bns = synth.cnn_weights(98, channels=16)
     rng = np.random.default_rng(99)
@@ -67,7 +67,7 @@ def _consensus(oracle):
     return cons
 
 
-def _worker(rank, world, port, out):
+def _worker(rank, world, nt, port, out):
     import torch
     import torch.distributed as dist
 
@@ -76,7 +76,7 @@ def _worker(rank, world, port, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        scan, y, lam, layers = _problem()
+        scan, y, lam, layers = _problem(nt)
         ang = scan.angles()
         lo, hi = timesplit.frame_blocks(scan.nt, world)[rank]
         n = scan.n
@@ -110,22 +110,25 @@ def _free_port():
     return port
 
 
-def test_two_gloo_ranks_match_the_whole_problem():
+# two ranks: ragged blocks of 3 and 2 frames, each rank with one neighbour;
+# three ranks: blocks of 2, the middle rank receiving halos from both sides
+@pytest.mark.parametrize("world,nt", [(2, 5), (3, 6)])
+def test_gloo_ranks_match_the_whole_problem(world, nt):
     import multiprocessing as mp
 
     import oracle
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, nt, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    got = sorted((q.get(timeout=600) for _ in range(2)), key=lambda t: t[0])
+    got = sorted((q.get(timeout=600) for _ in range(world)), key=lambda t: t[0])
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
     # the whole problem in one process
-    scan, y, lam, layers = _problem()
+    scan, y, lam, layers = _problem(nt)
     n = scan.n
     agents = [lambda w, x: oracle.prox_data(y, lam, w, x, scan, SIGMA, N_CG)]
     agents += [lambda w, x, o=o: oracle.denoise(w, layers, o) for o in ORIENTS]
