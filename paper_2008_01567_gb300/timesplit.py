@@ -13,7 +13,7 @@ The q-GGMRF prior of the plain method couples time-points inside every ICD
 sweep and is not split here.
 
 The module is host logic only.  The agents and the consensus are callables, so
-the same step runs the CUDA path (msf_prox_data on the rank's frames,
+the same step runs the CUDA path (GpuRank: msf_prox_data on the rank's frames,
 msf_denoise on the halo-extended block, msf_mace_consensus) and, in the tests,
 the FP64 oracle.  TorchComm carries the halos and the sum over
 torch.distributed: gloo for CPU tensors, NCCL for CUDA tensors.
@@ -121,3 +121,52 @@ def split_step(W, X, data_agent, prior_agents, consensus, mu, rho, lo: int, hi: 
     s = comm.allreduce_sum(torch.tensor([num, den], dtype=torch.float64, device=W.device))
     num, den = float(s[0]), float(s[1])
     return math.sqrt(num / den) if den > 0 else math.sqrt(num)
+
+
+class GpuRank:
+    """This rank's agents for split_step on its GPU, through the C ABI: the
+    data agent on frames [lo, hi) with a projector plan for those frames'
+    views, the three CNN agents (xy-t, yz-t, zx-t) on the halo-extended
+    blocks, and the consensus of msf_mace_consensus.
+
+    msf: the binding module; scan: the whole problem's scan (synth.Scan-like);
+    y, lam: this rank's measurements [hi - lo, views, nv, nu] on the device;
+    cnn: this rank's msf.Cnn handle (its workspace must not be shared with
+    another rank that runs at the same time)."""
+
+    def __init__(self, msf, scan, lo: int, hi: int, y, lam, cnn, sigma: float, n_cg: int, angles=None):
+        import dataclasses
+
+        import numpy as np
+        import torch
+        ang = np.asarray(scan.angles() if angles is None else angles, dtype=np.float64)
+        self.msf, self.lo, self.hi = msf, lo, hi
+        self.proj = msf.Projector(dataclasses.replace(scan, nt=hi - lo), angles=ang[lo:hi])
+        self.dp = msf.DataProx(self.proj)
+        self.y, self.lam, self.cnn = y, lam, cnn
+        self.sigma, self.n_cg = sigma, n_cg
+        v = self.proj.vol
+        self.shape = (v.nx, v.ny, v.nz, v.voxel)
+        self.work = torch.zeros(msf.MSF_CONSENSUS_WORK, dtype=torch.float64, device="cuda")
+
+    def data_agent(self, w0, x0):
+        self.msf.msf_prox_data(self.dp, self.y, self.lam, w0, x0, self.sigma, self.n_cg)
+        return x0
+
+    def prior_agents(self):
+        return [self._cnn_agent(o) for o in (0, 1, 2)]
+
+    def _cnn_agent(self, orient: int):
+        import torch
+        nx, ny, nz, voxel = self.shape
+
+        def agent(w_ext, n_before):
+            out = torch.empty_like(w_ext)
+            self.msf.msf_denoise(self.cnn, orient, self.msf.msf_vol(nx, ny, nz, w_ext.shape[0], voxel), w_ext, out)
+            return out[n_before:n_before + (self.hi - self.lo)]
+        return agent
+
+    def consensus(self, W, X, mu, rho):
+        self.msf.msf_mace_consensus(W, X, mu, rho, self.work)
+        s = self.work[self.msf.MSF_CONSENSUS_SUMS:self.msf.MSF_CONSENSUS_SUMS + 2].cpu()
+        return float(s[0]), float(s[1])

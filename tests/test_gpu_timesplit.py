@@ -109,3 +109,92 @@ def test_consensus_arguments(M):
         M.msf_mace_consensus(W, W.clone(), [0.75, 0.5], 0.5, work)             # weights do not sum to 1
     with pytest.raises(ValueError):
         M.msf_mace_consensus(W, W.clone(), [0.5, 0.5], 0.5, work[:10])         # workspace too small
+
+
+class _ThreadComm:
+    """Two emulated ranks as threads of one process: halos through queues
+    (cloned when sent, so later kernels of the sender cannot change them) and
+    the sum through a barrier."""
+
+    def __init__(self, rank, world, mail, barrier, sums):
+        self.rank, self.world = rank, world
+        self.mail, self.barrier, self.sums = mail, barrier, sums
+
+    def exchange(self, to_prev, to_next, n_prev, n_next, like):
+        if to_prev is not None:
+            self.mail[(self.rank, self.rank - 1)].put(to_prev.clone())
+        if to_next is not None:
+            self.mail[(self.rank, self.rank + 1)].put(to_next.clone())
+        before = self.mail[(self.rank - 1, self.rank)].get(timeout=60) if self.rank > 0 and n_prev else None
+        after = self.mail[(self.rank + 1, self.rank)].get(timeout=60) if self.rank + 1 < self.world and n_next else None
+        return before, after
+
+    def allreduce_sum(self, t):
+        self.sums[self.rank] = t.clone()
+        self.barrier.wait(timeout=60)
+        total = sum(self.sums[r] for r in range(self.world))
+        self.barrier.wait(timeout=60)
+        return total
+
+
+def test_gpu_rank_agents_in_split_step(M):
+    # timesplit.GpuRank + split_step, the two ranks as threads, against
+    # msf_mace_step on the whole problem: bit-identical states
+    import queue
+    import threading
+
+    import torch
+    scan = synth.Scan(n=24, nt=4, nu=32, nv=32, views=12)
+    n, nt = scan.n, scan.nt
+    _, counts, _, _ = measurement(scan, 81)
+    convs, bns = synth.cnn_weights(82)
+    flat = M.pack_params(convs, bns)
+    c = _t(counts)
+    y, lam = torch.empty_like(c), torch.empty_like(c)
+    M.msf_weights(c, y, lam, I0, I0)
+    cnn = M.Cnn(n ** 3 * nt)
+    cnn.set_params(flat)
+    P = M.Projector(scan)
+    W = torch.zeros((4, nt, n, n, n), device="cuda")
+    X = torch.zeros_like(W)
+    m = M.Mace(P, W, X, y, lam, M.MSF_PRIOR_CNN, cnn=cnn)
+    res = [M.msf_mace_step(m, RHO, SIGMA, MU, N_CG) for _ in range(ITERS)]
+    torch.cuda.synchronize()
+    world = 2
+    blocks = timesplit.frame_blocks(nt, world)
+    mail = {(a, b): queue.Queue() for a in range(world) for b in range(world)}
+    barrier, sums = threading.Barrier(world), {}
+    states, results, errors = {}, {}, []
+    ranks = []
+    for r, (lo, hi) in enumerate(blocks):
+        cr = M.Cnn(n ** 3 * nt)           # one workspace per rank
+        cr.set_params(flat)
+        ranks.append(timesplit.GpuRank(M, scan, lo, hi, y[lo:hi].contiguous(), lam[lo:hi].contiguous(), cr,
+                                       SIGMA, N_CG))
+
+    def run(r):
+        try:
+            lo, hi = blocks[r]
+            g = ranks[r]
+            Wr = torch.zeros((4, hi - lo, n, n, n), device="cuda")
+            Xr = torch.zeros_like(Wr)
+            comm = _ThreadComm(r, world, mail, barrier, sums)
+            results[r] = [timesplit.split_step(Wr, Xr, g.data_agent, g.prior_agents(), g.consensus, MU, RHO, lo, hi,
+                                               nt, comm) for _ in range(ITERS)]
+            torch.cuda.synchronize()
+            states[r] = (Wr, Xr)
+        except Exception as e:            # reported below, with the barrier released
+            errors.append(e)
+            barrier.abort()
+
+    threads = [threading.Thread(target=run, args=(r,)) for r in range(world)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=90)
+    assert not errors, errors
+    Ws = torch.cat([states[r][0] for r in range(world)], dim=1)
+    Xs = torch.cat([states[r][1] for r in range(world)], dim=1)
+    assert torch.equal(Ws, W) and torch.equal(Xs, X)
+    for r in range(world):
+        np.testing.assert_allclose(results[r], res, rtol=1e-12)
