@@ -321,20 +321,36 @@ def make_batch(params, seed, learned):
     return out
 
 
-def batch_throughput(params, seed, args, dist):
-    """Aggregate problem-iterations/s of the learned batch (one captured graph per iteration)."""
+def batch_run(params, seed, args, dist, world):
+    """The 12 uneven problems for both priors: per-problem NRMSE of X_0 after
+    exactly args.iters iterations from W = X = 0 (untimed), then the aggregate
+    problem-iterations/s of further batch iterations (one captured graph per
+    batch iteration), timed."""
+    import torch
     from paper_2008_01567_gb300 import msf
-    items = make_batch(params, seed + 1000, True)
-    B = msf.MaceBatch([it["m"] for it in items])
-    prms = [it["prm"] for it in items]
-    ms = timed(lambda: msf.msf_mace_batch_step(B, prms, want_residuals=False), max(1, args.steps), 2, dist)
-    n = len(items)
-    voxels = sum(it["scan"].nt * it["scan"].n ** 3 for it in items)
-    res = {"problems": n, "problem_iters_per_s": n * max(1, args.steps) / (ms / 1e3),
-           "batch_iters_per_s": max(1, args.steps) / (ms / 1e3), "voxels": voxels,
-           "ms_per_batch_iter": ms / max(1, args.steps)}
-    B.close()
-    return res
+    out = {}
+    for name, learned in (("learned", True), ("plain", False)):
+        items = make_batch(params, seed + 1000, learned)
+        B = msf.MaceBatch([it["m"] for it in items])
+        prms = [it["prm"] for it in items]
+        for _ in range(args.iters):
+            msf.msf_mace_batch_step(B, prms, want_residuals=False)
+        torch.cuda.synchronize()
+        nr = [(torch.linalg.vector_norm(it["X"][0] - it["prob"]["x_true"]) /
+               torch.linalg.vector_norm(it["prob"]["x_true"])).item() for it in items]
+        steps = max(1, args.steps)
+        ms = timed(lambda: msf.msf_mace_batch_step(B, prms, want_residuals=False), steps, 1, dist)
+        voxels = sum(it["scan"].nt * it["scan"].n ** 3 for it in items)
+        out[name] = {"problem_iters_per_s": world * len(items) * steps / (ms / 1e3),
+                     "ms_per_batch_iter": ms / steps, "voxels": voxels,
+                     "nrmse_at_iters": args.iters, "nrmse": [round(x, 4) for x in nr]}
+        B.close()
+        del items, B
+        torch.cuda.empty_cache()
+    ln, pn = out["learned"]["nrmse"], out["plain"]["nrmse"]
+    out["problems"] = len(ln)
+    out["learned_not_worse"] = sum(a <= b for a, b in zip(ln, pn))
+    return out
 
 
 def train_small(args, seed):
@@ -465,6 +481,109 @@ def run_sweep(args, rank, world, dist, seed):
     return None
 
 
+# ---------------------------------------------------------------- quality runs
+
+QUALITY_POINTS = (10, 20, 30, 60)   # iterations at which NRMSE and the residual are recorded
+
+
+def quality_run(step, X0, x_true, iters, points=QUALITY_POINTS):
+    """Runs `step` (one MACE iteration returning the consensus residual) from the
+    state it is given (W = X = 0) for max(iters, points) iterations, untimed and
+    separate from the throughput measurements.  Records NRMSE of X_0 and the
+    residual at every point, and NRMSE / PSNR / SSIM at exactly `iters`."""
+    from paper_2008_01567_gb300 import metrics
+    pts = sorted(set(p for p in points) | {iters})
+    traj, at = [], None
+    for it in range(1, pts[-1] + 1):
+        res = step(want_residual=it in pts)
+        if it in pts:
+            traj.append({"iter": it, "nrmse": round(metrics.nrmse(X0, x_true), 5), "residual": res})
+        if it == iters:
+            at = {"iters": iters, "nrmse": metrics.nrmse(X0, x_true), "psnr_db": round(metrics.psnr(X0, x_true), 2),
+                  "ssim": round(metrics.ssim(X0, x_true), 4), "residual": res}
+    return at, traj
+
+
+# ---------------------------------------------------------------- projector against its binding roof
+
+SMS, FP32_LANES, L1_BYTES_PER_CLK = 152, 128, 128   # per SM: FP32 lanes, L1 / shared-memory bytes per clock
+
+# Per in-grid ray-plane crossing (counted from the kernels' inner loops):
+#   forward: two 8-byte loads of the z-paired copies (16 B through the L1 data
+#     pipe) and 11.5 FP32-pipe instructions (per ray: the z crossing (FMA),
+#     its floor and fraction, three lerps of a subtraction and an FMA, the
+#     accumulation; the a crossing's FMA, floor and fraction shared by 2 rays);
+#   adjoint: each crossing is gathered by the two voxel runs holding its a taps;
+#     per visit a 4-byte sinogram load and two shared-memory read-modify-writes
+#     of the accumulators (20 B), and 12 FP32-pipe instructions.
+PROJ_MODEL = {"joseph_fwd": {"bytes": 16.0, "instr": 11.5},
+              "joseph_adj": {"bytes": 40.0, "instr": 24.0}}
+
+
+def in_grid_crossings(scan) -> int:
+    """Number of ray-plane crossings whose bilinear taps can touch the grid
+    (major-axis planes 0..n-1 where both minor crossings lie in [-1, n)), summed
+    over every ray of the scan, from the same FP64 ray constants as the
+    projector's column table.  Host-side bookkeeping for the roofline only."""
+    n, vox, du, dv = scan.n, scan.vox, scan.pitch, scan.pitch
+    u = (np.arange(scan.nu) - 0.5 * (scan.nu - 1)) * du
+    v = (np.arange(scan.nv) - 0.5 * (scan.nv - 1)) * dv
+    c0 = 0.5 * (n - 1)
+
+    def krange(f0, b, lo, hi):
+        inside = (f0 >= lo) & (f0 < hi)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            k1, k2 = (lo - f0) / b + c0, (hi - f0) / b + c0
+        kl = np.where(b != 0, np.minimum(k1, k2), np.where(inside, -np.inf, np.inf))
+        kh = np.where(b != 0, np.maximum(k1, k2), np.where(inside, np.inf, -np.inf))
+        return kl, kh
+
+    total = 0
+    for th in scan.angles().ravel():
+        c, s = math.cos(th), math.sin(th)
+        sx, sy = scan.dso * c, scan.dso * s
+        dx = -(scan.dsd - scan.dso) * c - u * s - sx
+        dy = -(scan.dsd - scan.dso) * s + u * c - sy
+        xm = np.abs(dx) >= np.abs(dy)
+        dmaj, smaj = np.where(xm, dx, dy), np.where(xm, sx, sy)
+        da, sa = np.where(xm, dy, dx), np.where(xm, sy, sx)
+        lam0 = -smaj / dmaj
+        al, ah = krange((sa + lam0 * da) / vox + c0, da / dmaj, -1.0, n)
+        zl, zh = krange(v[:, None] * (lam0 / vox)[None, :] + c0, v[:, None] / dmaj[None, :], -1.0, n)
+        lo = np.maximum(np.maximum(al[None, :], zl), 0.0)
+        hi = np.minimum(np.minimum(ah[None, :], zh), n - 1.0)
+        total += int(np.clip(np.floor(hi) - np.ceil(lo) + 1, 0, None).sum())
+    return total
+
+
+def projector_roofline(scan, fwd_ms, adj_ms, sm_mhz, peaks):
+    """Both projector kernels against (i) the HBM roof with algorithmic bytes
+    4(N + M) and (ii) their binding on-chip roof: the larger of the FP32-pipe
+    floor (instructions x crossings / (SMs x 128 lanes x clock)) and the L1 /
+    shared-memory floor (bytes x crossings / (SMs x 128 B x clock)), at the
+    median SM clock measured under load."""
+    N = scan.nt * scan.n ** 3
+    M = scan.nt * scan.views * scan.nv * scan.nu
+    X = in_grid_crossings(scan)
+    f = (sm_mhz or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    alu_peak = SMS * FP32_LANES * f            # FP32-pipe instructions per second
+    l1_peak = SMS * L1_BYTES_PER_CLK * f       # bytes per second
+    out = {"crossings_in_grid": X, "crossings_nominal": scan.nt * scan.views * scan.nu * scan.nv * scan.n,
+           "sm_mhz": f / 1e6, "fp32_peak_tinstr_s": alu_peak / 1e12, "l1_peak_TBps": l1_peak / 1e12,
+           "hbm_peak_GBps": peaks.get("hbm_gbs")}
+    for name, ms in (("joseph_fwd", fwd_ms), ("joseph_adj", adj_ms)):
+        m = PROJ_MODEL[name]
+        t_alu = m["instr"] * X / alu_peak * 1e3
+        t_l1 = m["bytes"] * X / l1_peak * 1e3
+        hbm = 4.0 * (N + M) / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "G_crossings_per_s": X / (ms / 1e3) / 1e9,
+                     "hbm_GBps_alg": hbm, "hbm_frac": hbm / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                     "fp32_floor_ms": t_alu, "l1_floor_ms": t_l1,
+                     "binding": "l1" if t_l1 >= t_alu else "fp32",
+                     "binding_frac": max(t_alu, t_l1) / ms}
+    return out
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -513,10 +632,6 @@ def main():
     P = prob["P"]
     tuned = msf.msf_projector_autotune(P)
     N = scan.nt * scan.n ** 3
-    total_iters = max(args.iters, args.warmup + args.steps)
-
-    def nrmse(x):
-        return (torch.linalg.vector_norm(x - prob["x_true"]) / torch.linalg.vector_norm(prob["x_true"])).item()
 
     # ---------------- the learned agents: trained on the GPU (untimed) on phantoms of other seeds
     tscan = synth.Scan(n=128, nt=4, nu=8, nv=8, views=1)
@@ -548,9 +663,14 @@ def main():
     X = torch.zeros(shape, device="cuda")
     m = msf.Mace(P, W, X, prob["y"], prob["lam"], msf.MSF_PRIOR_CNN, cnn=cnn)
 
-    def step():
-        msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0, want_residual=False)
+    def step(want_residual=False):
+        return msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0, want_residual=want_residual)
 
+    # quality: exactly args.iters iterations from W = X = 0, untimed (the
+    # trajectory continues to the last of QUALITY_POINTS)
+    q_learned, traj_learned = quality_run(step, X[0], prob["x_true"], args.iters)
+
+    # throughput (the iteration's cost does not depend on the state)
     for _ in range(args.warmup):
         step()
     clocks = Clocks(local)
@@ -563,7 +683,6 @@ def main():
     prof = msf.msf_profile_read()
     launches = sum(v[0] for v in prof.values())
     value = world * args.steps / (ms / 1e3)
-    done = args.warmup + args.steps
 
     e2e = None
     if not args.no_e2e:
@@ -575,25 +694,16 @@ def main():
             msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0, want_residual=True)
 
         e2e_ms = timed(e2e_step, args.steps, 0, dist)
-        done += args.steps
         e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": "MACE iters/s",
                "h2d_bytes_per_step": ch.numel() * 4, "d2h_bytes_per_step": 8}
-    while done < total_iters:
-        step()
-        done += 1
-    res = msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0)
     # the same iteration replayed as one CUDA graph
     gms = timed(lambda: msf.msf_mace_step(m, L["rho"], L["sigma"], L["mu"], L["n_cg"], 0, want_residual=False,
                                           use_graph=True), args.steps, 1, dist)
-    from paper_2008_01567_gb300 import metrics
-    learned = {"iters_per_s": value, "graph_iters_per_s": world * args.steps / (gms / 1e3), "nrmse": nrmse(X[0]),
-               "psnr_db": round(metrics.psnr(X[0], prob["x_true"]), 2),
-               "ssim": round(metrics.ssim(X[0], prob["x_true"]), 4),
-               "residual": res, "iters": done + 1 + args.steps + 1}
+    learned = {"iters_per_s": value, "graph_iters_per_s": world * args.steps / (gms / 1e3),
+               "quality": q_learned, "trajectory": traj_learned}
+    m.close()
     del m, W, X
-    batch = None
-    if not args.no_batch:
-        batch = batch_throughput(cnn.get_params(), seed, args, dist)
+    torch.cuda.empty_cache()
 
     # ---------------- plain q-GGMRF MACE at the same size
     s = PLAIN
@@ -602,20 +712,24 @@ def main():
     mrf = msf.msf_mrf(2.0, s["q"], s["T"], s["sx"], s["bt"])
     m2 = msf.Mace(P, W2, X2, prob["y"], prob["lam"], msf.MSF_PRIOR_QGGMRF, mrf=mrf)
 
-    def pstep():
-        msf.msf_mace_step(m2, s["rho"], s["sigma"], s["mu"], s["n_cg"], s["n_sweeps"], want_residual=False)
+    def pstep(want_residual=False):
+        return msf.msf_mace_step(m2, s["rho"], s["sigma"], s["mu"], s["n_cg"], s["n_sweeps"],
+                                 want_residual=want_residual)
 
+    q_plain, traj_plain = quality_run(pstep, X2[0], prob["x_true"], args.iters)
     for _ in range(args.warmup):
         pstep()
     pms = timed(pstep, args.steps, 0, dist)
-    for _ in range(total_iters - args.warmup - args.steps):
-        pstep()
-    pres = msf.msf_mace_step(m2, s["rho"], s["sigma"], s["mu"], s["n_cg"], s["n_sweeps"])
     plain = {"iters_per_s": world * args.steps / (pms / 1e3), "ms_per_iter": pms / args.steps,
-             "nrmse": nrmse(X2[0]), "psnr_db": round(metrics.psnr(X2[0], prob["x_true"]), 2),
-             "ssim": round(metrics.ssim(X2[0], prob["x_true"]), 4),
-             "residual": pres, "iters": total_iters + 1, "sigma_x": s["sx"]}
+             "quality": q_plain, "trajectory": traj_plain, "sigma_x": s["sx"]}
+    m2.close()
     del m2, W2, X2
+    torch.cuda.empty_cache()
+
+    # ---------------- the queue of 12 uneven problems: per-problem NRMSE, learned vs plain
+    batch = None
+    if not args.no_batch:
+        batch = batch_run(cnn.get_params(), seed, args, dist, world)
 
     # ---------------- projector throughput (one launch each, algorithmic bytes)
     yb = torch.empty_like(prob["y"])
@@ -628,15 +742,9 @@ def main():
     torch.cuda.synchronize()
     msf.msf_profile_enable(False)
     pp = msf.msf_profile_read()
-    M = yb.numel()
     fwd_ms = pp["joseph_fwd"][1] / pp["joseph_fwd"][0]
     adj_ms = pp["joseph_adj"][1] / pp["joseph_adj"][0]
-    steps_per_launch = scan.nt * scan.views * scan.nu * scan.nv * scan.n   # ray-plane crossings
-    projector = {"fwd_ms": fwd_ms, "adj_ms": adj_ms,
-                 "fwd_GBps_alg": 4.0 * (N + M) / (fwd_ms / 1e3) / 1e9,
-                 "adj_GBps_alg": 4.0 * (N + M) / (adj_ms / 1e3) / 1e9,
-                 "fwd_Gcrossings_per_s": steps_per_launch / (fwd_ms / 1e3) / 1e9,
-                 "adj_Gcrossings_per_s": steps_per_launch / (adj_ms / 1e3) / 1e9}
+    projector = projector_roofline(scan, fwd_ms, adj_ms, ck.get("sm_mhz"), peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -654,7 +762,11 @@ def main():
                            "l2": "inputs larger than L2 (3.6 GB per 4D volume)"},
                 "roofline": roofline(prof, scan, 4, peaks, args.steps),
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
-                "learned": learned, "plain": plain, "training": training, "projector": projector,
+                "learned": learned, "plain": plain,
+                "learned_vs_plain": {"iters": args.iters,
+                                     "nrmse_learned": q_learned["nrmse"], "nrmse_plain": q_plain["nrmse"],
+                                     "learned_not_worse": q_learned["nrmse"] <= q_plain["nrmse"]},
+                "training": training, "projector": projector,
                 "projector_tuning": {"fwd_block": list(tuned[:2]), "adj_zrun": tuned[2]}, "batch": batch,
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()}}
         print(json.dumps(line))

@@ -155,7 +155,10 @@ msf_status msf_backproject(msf_projector* p, const float* d_y, float* d_x, void*
  * device current); make that first call before any stream capture.  All calls
  * share the one array and each call overwrites it, so calls that may overlap
  * on the GPU (different streams, different host threads) race and must be
- * serialised by the caller.  Same layouts and result as msf_project. */
+ * serialised by the caller.  Same layouts as msf_project, and the same result
+ * bit for bit (the same FP32 operations per crossing, in the same order).
+ * Every (view, column) is checked on the host before any work is enqueued;
+ * geometries that msf_projector_create rejects return MSF_ERR_ARG here too. */
 msf_status msf_project_static(const msf_geom* geom, const msf_vol* vol, const float* d_x, float* d_y,
                               void* stream);
 

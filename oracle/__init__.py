@@ -6,10 +6,11 @@ leg may import it.  It shares no code with the CUDA path; the loop-heavy parts
 (projector, phantom, q-GGMRF ICD) are plain C in oracle.c, the rest is numpy in
 float64 written in the paper's order and notation.
 
-Every function names the passage it follows.  Readings of points the paper leaves
-open (projector model, CNN depth and width, temporal edges, ...) are listed in
-the design doc.  All functions here are pinned by tests under tests/ against closed
-forms, invariants, brute force or library routines; none is marked unpinned.
+Every function names the passage it follows, and states in its docstring the
+reading it takes where the paper leaves a point open (projector model, CNN
+depth and width, temporal edges, ...).  All functions here are pinned by tests
+under tests/ against closed forms, invariants, brute force or library routines;
+none is marked unpinned.
 """
 from __future__ import annotations
 

@@ -981,8 +981,12 @@ static_assert(STATIC_MAX_VIEWS * 8 + STATIC_MAX_COLUMNS * 32 + STATIC_MAX_VIEWS 
               "static scratch too small for its stated limits");
 
 // Joseph forward projection reading the frame [nz][ny][nx] for both ray
-// families (same interpolation arithmetic as joseph_fwd_kernel; only the
-// addressing of x-major rays differs).
+// families.  Per crossing it performs the forward's operations with the same
+// explicit roundings (the lerp v00 + w_a (v01 - v00) along a, then along z,
+// and a round-to-nearest accumulation over increasing planes), and a plane
+// whose taps all lie outside the grid adds exactly zero in joseph_fwd_kernel,
+// so the result equals msf_project's bit for bit; only the addressing differs
+// (x-major rays read x-strided data here instead of the transposed copy).
 __global__ void __launch_bounds__(128) joseph_fwd_direct_kernel(const float* __restrict__ x,
                                                                 const float4* __restrict__ col,
                                                                 float* __restrict__ out, ProjDims d) {
@@ -1016,10 +1020,11 @@ __global__ void __launch_bounds__(128) joseph_fwd_direct_kernel(const float* __r
         const float v01 = (z_in0 && a_in1) ? __ldg(p00 + s_min) : 0.0f;
         const float v10 = (z_in1 && a_in0) ? __ldg(p00 + s_z) : 0.0f;
         const float v11 = (z_in1 && a_in1) ? __ldg(p00 + s_z + s_min) : 0.0f;
-        const float wa0 = __fsub_rn(1.0f, wa1), wz0 = __fsub_rn(1.0f, wz1);
-        acc += wz0 * (wa0 * v00 + wa1 * v01) + wz1 * (wa0 * v10 + wa1 * v11);
+        const float top = __fmaf_rn(wa1, __fsub_rn(v01, v00), v00);
+        const float bot = __fmaf_rn(wa1, __fsub_rn(v11, v10), v10);
+        acc = __fadd_rn(acc, __fmaf_rn(wz1, __fsub_rn(bot, top), top));
     }
-    out[((size_t)g * d.nv + iv) * d.nu + iu] = acc * rz.step;
+    out[((size_t)g * d.nv + iv) * d.nu + iu] = __fmul_rn(acc, rz.step);
 }
 
 // Device address of g_static_scratch for each device, looked up once per
@@ -1046,13 +1051,18 @@ extern "C" msf_status msf_project_static(const msf_geom* geom, const msf_vol* vo
                 "msf_project_static: source and detector must lie outside the volume's circumscribed cylinder");
     MSF_REQUIRE(0.5 * (geom->nv - 1) * geom->dv < geom->dsd / sqrt(2.0),
                 "msf_project_static: cone too wide (z-major rays are not modelled)");
-    // the voxel planes of every ray must lie between its source and detector
-    // (checked here in FP64 on the host, so no device flag has to be read back)
+    // The voxel planes of every ray must lie between its source and detector.
+    // This is checked here in FP64 on the host for every (view, column) -- at
+    // most STATIC_MAX_COLUMNS evaluations -- with the formulas of
+    // column_table_kernel, so no device flag has to be read back (the table
+    // kernel still writes its flag into the array; nothing reads it).  Checking
+    // only the end columns would not do: where a view's columns switch between
+    // x-major and y-major, the first column of the inner segment can fail alone.
     for (long long g = 0; g < G; ++g) {
         const double th = geom->angles[g], c = cos(th), s = sin(th);
-        for (int iu = 0; iu < geom->nu; iu += geom->nu > 1 ? geom->nu - 1 : 1) {
+        const double sx = geom->dso * c, sy = geom->dso * s;
+        for (int iu = 0; iu < geom->nu; ++iu) {
             const double u = (iu - 0.5 * (geom->nu - 1)) * geom->du;
-            const double sx = geom->dso * c, sy = geom->dso * s;
             const double dx = -(geom->dsd - geom->dso) * c - u * s - sx, dy = -(geom->dsd - geom->dso) * s + u * c - sy;
             const bool xm = fabs(dx) >= fabs(dy);
             const double dmaj = xm ? dx : dy, smaj = xm ? sx : sy;
@@ -1060,7 +1070,8 @@ extern "C" msf_status msf_project_static(const msf_geom* geom, const msf_vol* vo
             const double l1 = (-0.5 * (nmaj - 1) * vol->voxel - smaj) / dmaj;
             const double l2 = (0.5 * (nmaj - 1) * vol->voxel - smaj) / dmaj;
             MSF_REQUIRE(fmin(l1, l2) > 0.0 && fmax(l1, l2) < 1.0,
-                        "msf_project_static: a ray's voxel planes are not all between its source and detector");
+                        "msf_project_static: a ray's voxel planes are not all between its source and detector "
+                        "(view %lld, column %d)", g, iu);
         }
     }
     int dev = 0;

@@ -62,6 +62,22 @@ def test_argument_errors_before_launch(lib):
     assert lib.msf_version().startswith(b"msf-gb300")
 
 
+def test_static_projection_checks_every_column(lib):
+    """msf_project_static checks on the host, before any device call, that the
+    voxel planes of every (view, column) lie between source and detector; the
+    geometry below fails on interior column 3 only (where the view's columns
+    switch from x-major to y-major), so an end-columns check would pass it."""
+    from paper_2008_01567_gb300 import msf
+    from tests.test_zz_no_alloc import INTERIOR_FAIL as g
+    ang = np.array([g["theta"]], dtype=np.float64)
+    geom = msf.msf_geom(g["nu"], g["nv"], 1, g["du"], g["du"], g["dso"], g["dsd"],
+                        ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    vol = msf.msf_vol(g["n"], g["n"], g["n"], 1, 1.0 / g["n"])
+    fake = ctypes.c_void_p(256)                    # never dereferenced: the checks come first
+    assert lib.msf_project_static(ctypes.byref(geom), ctypes.byref(vol), fake, fake, None) == 1
+    assert b"column 3" in lib.msf_last_error(), lib.msf_last_error()
+
+
 def test_binding_refuses_cpu_tensors(lib):
     torch = pytest.importorskip("torch")
     from paper_2008_01567_gb300 import msf

@@ -23,3 +23,39 @@ def test_clock_samples_empty():
 
 def test_replica_seeds_differ():
     assert len({bench.replica_seed(r) for r in range(8)}) == 8
+
+
+def test_in_grid_crossings_brute_force():
+    """The vectorised crossing count of the projector roofline against a
+    plane-by-plane enumeration of every ray on a small scan (both protocols)."""
+    import math
+
+    import numpy as np
+
+    from paper_2008_01567_gb300 import synth
+    for mode in ("sparse360", "wedge90"):
+        sc = synth.Scan(n=12, nt=2, nu=15, nv=11, views=3, mode=mode)
+        n, c0 = sc.n, 0.5 * (sc.n - 1)
+        brute = 0
+        for th in sc.angles().ravel():
+            c, s = math.cos(th), math.sin(th)
+            for iu in range(sc.nu):
+                u = (iu - 0.5 * (sc.nu - 1)) * sc.pitch
+                sx, sy = sc.dso * c, sc.dso * s
+                dx = -(sc.dsd - sc.dso) * c - u * s - sx
+                dy = -(sc.dsd - sc.dso) * s + u * c - sy
+                xm = abs(dx) >= abs(dy)
+                dmaj, smaj = (dx, sx) if xm else (dy, sy)
+                da, sa = (dy, sy) if xm else (dx, sx)
+                for iv in range(sc.nv):
+                    v = (iv - 0.5 * (sc.nv - 1)) * sc.pitch
+                    for k in range(n):
+                        lam = ((k - c0) * sc.vox - smaj) / dmaj
+                        fa = (sa + lam * da) / sc.vox + c0
+                        fz = lam * v / sc.vox + c0
+                        brute += (-1.0 <= fa < n) and (-1.0 <= fz < n)
+        got = bench.in_grid_crossings(sc)
+        # interval end points are rounded differently from the per-plane test:
+        # allow a crossing exactly on a boundary to fall either way
+        assert abs(got - brute) <= max(2, brute // 1000), (mode, got, brute)
+        assert 0 < got < sc.nt * sc.views * sc.nu * sc.nv * n

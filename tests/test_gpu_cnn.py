@@ -137,6 +137,38 @@ def test_full_size_sampled_slices(M):
         assert rel_l2(cen - got, cen - ref) <= 1e-2, o
 
 
+def test_inference_workload_sampled_slices(M):
+    # the learned-agent inference workload: 256 x 256 slices x 16 time-points
+    # (a 256^3 x 16 volume, so every orientation's slices are 256 x 256), two
+    # sampled slices of each orientation, among them the first and the last
+    # time-points where the 5-frame window is clamped
+    import torch
+    n, nt = 256, 16
+    convs, bns, stats = _net(59)
+    c, layers = _gpu_net(M, convs, bns, stats, n ** 3)
+    scan = synth.Scan(n=n, nt=nt, nu=8, nv=8, views=1)
+    P = M.Projector(scan)
+    x = torch.empty((nt, n, n, n), device="cuda")
+    M.msf_phantom_voxelize(P.vol, synth.ellipsoids(60, 6, scan), x, ss=1)
+    x += 0.05 * torch.randn(x.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(6))
+    out = torch.empty_like(x)
+    samples = {"xy": ((0, 128), (11, 3)), "yz": ((15, 200), (6, 255)), "zx": ((1, 64), (9, 130))}
+    for o, picks in samples.items():
+        M.msf_denoise(c, ORIENT[o], P.vol, x, out)
+        torch.cuda.synchronize()
+        for t, s in picks:
+            tw = np.clip(np.arange(t - 2, t + 3), 0, nt - 1)
+            if o == "xy":
+                img, got, cen = x[tw, s], out[t, s], x[t, s]
+            elif o == "yz":
+                img, got, cen = x[tw, :, :, s], out[t, :, :, s], x[t, :, :, s]
+            else:
+                img, got, cen = x[tw, :, s, :].transpose(1, 2), out[t, :, s, :].T, x[t, :, s, :].T
+            img, got, cen = img.cpu().numpy(), got.cpu().numpy(), cen.cpu().numpy()
+            ref = oracle.cnn_forward(img[None].astype(np.float64), layers, emulate_bf16=True)[0]
+            assert rel_l2(cen - got, cen - ref) <= 1e-2, (o, t, s)
+
+
 def test_denoise_argument_errors(M):
     c = M.Cnn(1000)
     vol = M.msf_vol(16, 16, 16, 2, 1.0)

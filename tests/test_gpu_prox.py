@@ -59,6 +59,34 @@ def test_cg_prox_matches_oracle(M, scan, n_cg):
     assert rel_l2(z0, ref) > 1e-2
 
 
+@pytest.mark.parametrize("scan", [synth.PROJ, synth.PROJ_WEDGE], ids=["sparse360", "wedge90"])
+def test_cg_prox_projector_workload_frames(M, scan):
+    # the projector workload (128^3 x 8, 192 x 160 detector, 32 views per
+    # time-point, both protocols) with 10 CG iterations: the GPU solves all
+    # eight frames in its production launch shapes (the CG partial sums and
+    # z-runs at their full-size grids); the oracle solves the first and the
+    # last frame on its own (the solves are independent per frame)
+    n_cg, sigma = 10, 0.1
+    x0, counts, y, lam = measurement(scan, 36)
+    v = f32(x0 + synth.normal(37, x0.shape, 0.05))
+    z0 = f32(0.5 * x0)
+    P = M.Projector(scan)
+    M.msf_projector_autotune(P)
+    dp = M.DataProx(P)
+    c = _t(counts)
+    yg, lg = _t(np.zeros_like(counts)), _t(np.zeros_like(counts))
+    M.msf_weights(c, yg, lg, I0, I0)
+    z = _t(z0)
+    M.msf_prox_data(dp, yg, lg, _t(v), z, sigma, n_cg)
+    got = z.cpu().numpy()
+    ang = scan.angles()
+    yf, lf = f32(y), f32(lam)
+    for t in (0, scan.nt - 1):
+        ref = oracle.prox_data_frame(yf[t], lf[t], v[t], z0[t], scan, ang[t], sigma, n_cg)
+        assert rel_l2(got[t], ref) <= 2 * n_cg * 1e-5, t
+        assert rel_l2(z0[t], ref) > 1e-2
+
+
 def test_cg_zero_iterations_is_identity(M):
     scan = synth.TINY
     P = M.Projector(scan)
