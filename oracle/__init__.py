@@ -53,6 +53,7 @@ def _L():
         lib.or_qggmrf_cost.argtypes = [P, I, I, I, I, D, D, D, D, D]
         lib.or_qggmrf_cost.restype = D
         lib.or_qggmrf_icd.argtypes = [P, P, I, I, I, I, D, D, D, D, D, D, I]
+        lib.or_qggmrf_surrogate_lap.argtypes = [P, P, P, I, I, I, I, D, D, D, D, D]
         _lib = lib
     return _lib
 
@@ -174,6 +175,75 @@ def prox_data(y4, lam4, v4, z4, scan, sigma, n_cg):
                      for t in range(v4.shape[0])])
 
 
+def backproject_sq(y3: np.ndarray, scan, angles: np.ndarray, shape=None) -> np.ndarray:
+    """x_s = sum_r a_rs^2 y_r for one frame: the transpose of `project` with each
+    matrix entry squared (with y = Lambda, the diagonal of A^T Lambda A)."""
+    y3 = np.ascontiguousarray(y3, dtype=np.float64)
+    angles = np.ascontiguousarray(angles, dtype=np.float64)
+    nz, ny, nx = shape if shape is not None else (scan.n, scan.n, scan.n)
+    x = np.zeros((nz, ny, nx))
+    _L().or_project(_p(x), _p(y3), nx, ny, nz, scan.vox, scan.nu, scan.nv, scan.pitch,
+                    scan.pitch, scan.dso, scan.dsd, _p(angles), len(angles), 2)
+    return x
+
+
+def parity_groups(shape3) -> list:
+    """The eight voxel groups of the grouped ICD sweep: voxel (z, y, x) belongs to
+    group (pz*2 + py)*2 + px with (pz, py, px) = (z, y, x) mod 2; groups are
+    visited in increasing order.  Returned as boolean masks."""
+    z, y, x = np.meshgrid(*[np.arange(n) for n in shape3], indexing="ij")
+    key = ((z % 2) * 2 + (y % 2)) * 2 + (x % 2)
+    return [key == g for g in range(8)]
+
+
+def data_cost(y3, lam3, v3, z3, scan, angles, sigma) -> float:
+    """The cost of Eq. (4) with l of Eq. (2) for one frame:
+    1/2 ||y - A z||^2_Lambda + ||z - v||^2 / (2 sigma^2)."""
+    e = y3 - project(z3, scan, angles)
+    return 0.5 * float(np.sum(lam3 * e * e)) + float(np.sum((z3 - v3) ** 2)) / (2.0 * sigma ** 2)
+
+
+def prox_data_icd_frame(y3, lam3, v3, z3, scan, angles, sigma, n_sweeps, groups=None):
+    """Partial update L~(v; z) of Eq. (13) by iterative coordinate descent
+    (Sec. III takes L~ as a few ICD iterations), in a grouped order that a GPU
+    can run in parallel: each sweep visits the voxel groups in order; within a
+    group every voxel takes its own one-dimensional Newton step against the
+    same error sinogram,
+        theta1_s = -(A^T Lambda e)_s + (z_s - v_s)/sigma^2,
+        theta2_s = (A^T Lambda A)_ss + 1/sigma^2,     delta_s = -theta1_s/theta2_s,
+    (e = y - A z), and the group moves by alpha * delta, with alpha the exact
+    minimiser of the quadratic cost along delta,
+        alpha = -theta1.delta / (||A delta||^2_Lambda + ||delta||^2/sigma^2),
+    before e is updated and the next group is visited.  With one voxel per
+    group alpha = 1 and this is plain sequential ICD; with several it is a
+    descent step of the cost in every group.  groups: list of boolean masks
+    (default: the eight parity groups)."""
+    z = np.array(z3, dtype=np.float64)
+    if groups is None:
+        groups = parity_groups(z.shape)
+    e = y3 - project(z, scan, angles)
+    theta2 = backproject_sq(lam3, scan, angles, z.shape) + 1.0 / sigma ** 2
+    for _ in range(n_sweeps):
+        for g in groups:
+            theta1 = -backproject(lam3 * e, scan, angles, z.shape) + (z - v3) / sigma ** 2
+            delta = np.where(g, -theta1 / theta2, 0.0)
+            Ad = project(delta, scan, angles)
+            den = float(np.sum(lam3 * Ad * Ad)) + float(np.sum(delta * delta)) / sigma ** 2
+            if den <= 0.0:
+                continue
+            alpha = -float(np.sum(theta1 * delta)) / den
+            z += alpha * delta
+            e -= alpha * Ad
+    return z
+
+
+def prox_data_icd(y4, lam4, v4, z4, scan, sigma, n_sweeps):
+    """The grouped-ICD L~ for the 4D volume: one independent solve per time-point."""
+    ang = scan.angles()
+    return np.stack([prox_data_icd_frame(y4[t], lam4[t], v4[t], z4[t], scan, ang[t], sigma, n_sweeps)
+                     for t in range(v4.shape[0])])
+
+
 # Prior proximal map H(x) = argmin_z ||x - z||^2/(2 sigma^2) + h(z)   (Eq. (5)),
 # with h the 4D q-GGMRF MRF of Sec. VII (26 spatial + 2 temporal neighbours).
 
@@ -199,6 +269,65 @@ def prox_qggmrf(v4, z4, sigma, p, q, T, sx, bt, n_sweeps):
     nt, nz, ny, nx = v4.shape
     _L().or_qggmrf_icd(_p(v4), _p(z), nx, ny, nz, nt, sigma, p, q, T, sx, bt, n_sweeps)
     return z
+
+
+# The MBIR + 4D-MRF comparison of Sec. VI solved directly: the MAP estimate of
+# Eq. (3) with the q-GGMRF prior, without the MACE split.
+
+
+def surrogate_lap(anchor4, x4, p, q, T, sx, bt):
+    """(L_a x)_s = sum_r b_sr a(anchor_s - anchor_r) (x_s - x_r); 2 L_a x is the
+    gradient of the prior's quadratic surrogate built at `anchor` (see oracle.c)."""
+    a = np.ascontiguousarray(anchor4, dtype=np.float64)
+    x = np.ascontiguousarray(x4, dtype=np.float64)
+    out = np.zeros_like(x)
+    nt, nz, ny, nx = x.shape
+    _L().or_qggmrf_surrogate_lap(_p(a), _p(x), _p(out), nx, ny, nz, nt, p, q, T, sx, bt)
+    return out
+
+
+def map_cost(y4, lam4, x4, scan, p, q, T, sx, bt, beta) -> float:
+    """Phi(x) = l(x) + beta h(x) = 1/2 sum_t ||y_t - A x_t||^2_Lambda + beta h(x), the
+    MAP cost of Eq. (3) with the 4D q-GGMRF prior h of Sec. VII."""
+    e = y4 - project4d(x4, scan)
+    return 0.5 * float(np.sum(lam4 * e * e)) + beta * qggmrf_cost(x4, p, q, T, sx, bt)
+
+
+def map_mm(y4, lam4, x4, scan, p, q, T, sx, bt, beta, n_outer, n_cg):
+    """Direct MAP solve of Eq. (3), l(x) + beta h(x), by majorise-minimise: each
+    outer iteration replaces h by its symmetric-bound quadratic surrogate built
+    at the current x (equal to h there, above it elsewhere), and takes n_cg
+    conjugate-gradient steps, warm-started at x, on the surrogate problem
+        (A^T Lambda A + 2 beta L_a) x = A^T Lambda y
+    over the whole 4D volume (the prior couples the time-points, so the CG
+    scalars are global).  With MACE weights mu = (mu_0, mu_1) and exact agents
+    the consensus equilibrium of Sec. III is this MAP point with beta = mu_1/mu_0."""
+    x = np.array(x4, dtype=np.float64)
+    ang = scan.angles()
+    nt = x.shape[0]
+
+    def data_normal(v):
+        return np.stack([backproject(lam4[t] * project(v[t], scan, ang[t]), scan, ang[t], v[t].shape)
+                         for t in range(nt)])
+
+    for _ in range(n_outer):
+        anchor = x.copy()
+        r = np.stack([backproject(lam4[t] * (y4[t] - project(x[t], scan, ang[t])), scan, ang[t], x[t].shape)
+                      for t in range(nt)]) - 2.0 * beta * surrogate_lap(anchor, x, p, q, T, sx, bt)
+        d = r.copy()
+        rr = float(np.vdot(r, r))
+        for _ in range(n_cg):
+            qv = data_normal(d) + 2.0 * beta * surrogate_lap(anchor, d, p, q, T, sx, bt)
+            dq = float(np.vdot(d, qv))
+            if dq == 0.0:
+                break
+            alpha = rr / dq
+            x += alpha * d
+            r -= alpha * qv
+            rr_new = float(np.vdot(r, r))
+            d = r + (rr_new / rr if rr != 0.0 else 0.0) * d
+            rr = rr_new
+    return x
 
 
 # MACE operators.

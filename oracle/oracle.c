@@ -13,6 +13,9 @@
  *                         leaves its model to its cone-beam reference, so the rules
  *                         below are this project's reading (circular orbit, flat
  *                         detector, Joseph interpolation).
+ *                         Mode 2 is the transpose with squared weights,
+ *                         x_s = sum_r a_rs^2 y_r, the diagonal of A^T diag(y) A
+ *                         (the curvature that ICD divides by, Sec. III).
  *   or_ellipsoid_project  exact line integrals of a sum of uniform ellipsoids
  *                         (measurement simulation, Sec. VII-A: noisy data from the
  *                         projection of a phantom that moves one voxel per frame).
@@ -20,7 +23,8 @@
  *   or_qggmrf_*           q-GGMRF potential, its symmetric-bound surrogate
  *                         coefficient, and a 16-colour ICD solver for the prior
  *                         proximal map H(v) of Sec. III, Eq. (5) with the 4D MRF
- *                         prior of Sec. VII (26 spatial + 2 temporal neighbours).
+ *                         prior of Sec. VII (26 spatial + 2 temporal neighbours);
+ *                         the surrogate's Laplacian for the direct MAP solve.
  *
  * Geometry (all lengths in the caller's unit):
  *   voxel (ix,iy,iz) centre = ((ix-(nx-1)/2)*vox, (iy-(ny-1)/2)*vox, (iz-(nz-1)/2)*vox)
@@ -64,8 +68,10 @@ static or_ray ray_of(double th, int iu, int iv, int nu, int nv, double du, doubl
 
 /* Joseph sampling of one ray: visits every (voxel, weight) pair of the ray and
  * either gathers (adjoint == 0: returns sum w*x[v]) or scatters (adjoint == 1:
- * x[v] += w*val).  One routine for both directions makes A^T the literal
- * transpose of A. */
+ * x[v] += w*val; adjoint == 2: x[v] += w*w*val).  One routine for both
+ * directions makes A^T the literal transpose of A.  A ray meets a voxel on one
+ * plane only (the plane of the voxel's major-axis index), so w is the whole
+ * matrix entry a_rv and w*w its square. */
 static double joseph_ray(const or_ray* r, double* x, int nx, int ny, int nz, double vox,
                          int adjoint, double val)
 {
@@ -100,7 +106,8 @@ static double joseph_ray(const or_ray* r, double* x, int nx, int ny, int nz, dou
                 size_t idx = xmajor ? ((size_t)iz * ny + ia) * nx + k
                                     : ((size_t)iz * ny + k) * nx + ia;
                 double w = step * wa[ja] * wz[jz];
-                if (adjoint) x[idx] += w * val;
+                if (adjoint == 2) x[idx] += w * w * val;
+                else if (adjoint) x[idx] += w * val;
                 else acc += w * x[idx];
             }
         }
@@ -109,7 +116,8 @@ static double joseph_ray(const or_ray* r, double* x, int nx, int ny, int nz, dou
 }
 
 /* Forward (adjoint == 0): y[view][iv][iu] = (A x).  Adjoint (adjoint == 1):
- * x = A^T y (x is overwritten).  Angles in radians, one per view. */
+ * x = A^T y; adjoint == 2: x = (A.^2)^T y (x is overwritten in both).  Angles
+ * in radians, one per view. */
 void or_project(double* x, double* y, int nx, int ny, int nz, double vox,
                 int nu, int nv, double du, double dv, double dso, double dsd,
                 const double* angles, int nviews, int adjoint)
@@ -121,7 +129,7 @@ void or_project(double* x, double* y, int nx, int ny, int nz, double vox,
                 for (int iu = 0; iu < nu; ++iu) {
                     or_ray r = ray_of(angles[j], iu, iv, nu, nv, du, dv, dso, dsd);
                     double val = y[((size_t)j * nv + iv) * nu + iu];
-                    if (val != 0.0) joseph_ray(&r, x, nx, ny, nz, vox, 1, val);
+                    if (val != 0.0) joseph_ray(&r, x, nx, ny, nz, vox, adjoint, val);
                 }
         return;
     }
@@ -323,4 +331,42 @@ void or_qggmrf_icd(const double* v, double* z, int nx, int ny, int nz, int nt,
                             z[s] = num / den;
                         }
         }
+}
+
+/* The Laplacian of the symmetric-bound surrogate of h built at `anchor`:
+ *   out_s = sum_{r in N(s)} b_sr a(anchor_s - anchor_r) (x_s - x_r),
+ * over the 26 spatial and 2 temporal neighbours (free boundaries).  The
+ * surrogate Q(x) = sum over pairs b_sr a_sr (x_s - x_r)^2 majorises h up to a
+ * constant and touches it at the anchor; its gradient is 2 * out. */
+void or_qggmrf_surrogate_lap(const double* anchor, const double* x, double* out, int nx, int ny, int nz,
+                             int nt, double p, double q, double T, double sx, double bt)
+{
+    double bf, be, bc;
+    nb_weights(&bf, &be, &bc);
+    size_t fs = (size_t)nz * ny * nx;
+    for (int t = 0; t < nt; ++t)
+        for (int iz = 0; iz < nz; ++iz)
+            for (int iy = 0; iy < ny; ++iy)
+                for (int ix = 0; ix < nx; ++ix) {
+                    size_t s = (size_t)t * fs + ((size_t)iz * ny + iy) * nx + ix;
+                    double acc = 0.0;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                if (!dx && !dy && !dz) continue;
+                                int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+                                if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
+                                int m = abs(dx) + abs(dy) + abs(dz);
+                                double b = m == 1 ? bf : (m == 2 ? be : bc);
+                                size_t r = (size_t)t * fs + ((size_t)jz * ny + jy) * nx + jx;
+                                acc += b * or_qggmrf_coef(anchor[s] - anchor[r], p, q, T, sx) * (x[s] - x[r]);
+                            }
+                    for (int dt = -1; dt <= 1; dt += 2) {
+                        int tt = t + dt;
+                        if (tt < 0 || tt >= nt) continue;
+                        size_t r = s + (ptrdiff_t)dt * (ptrdiff_t)fs;
+                        acc += bt * or_qggmrf_coef(anchor[s] - anchor[r], p, q, T, sx) * (x[s] - x[r]);
+                    }
+                    out[s] = acc;
+                }
 }

@@ -61,6 +61,83 @@ def test_cg_energy_error_decreases(oracle):
         prev = en
 
 
+def test_backproject_sq_is_squared_transpose(oracle):
+    # (A.^2)^T y from the squared-weight scatter equals the dense columns squared
+    sc, y, lam = _tiny_problem(oracle, seed=5)
+    ang = sc.angles()[0]
+    shape = (4, 4, 4)
+    A = _dense_A(oracle, sc, ang, shape)
+    got = oracle.backproject_sq(lam[0], sc, ang, shape).ravel()
+    np.testing.assert_allclose(got, (A * A).T @ lam[0].ravel(), rtol=1e-12, atol=1e-14)
+
+
+def _icd_sequential(A, lam, y, v, z0, sigma, order, sweeps):
+    # textbook ICD on a dense system matrix: one voxel at a time, exact
+    # minimisation of the quadratic cost of Eq. (4) along that coordinate
+    z = z0.ravel().copy()
+    e = y.ravel() - A @ z
+    L = lam.ravel()
+    for _ in range(sweeps):
+        for s in order:
+            a = A[:, s]
+            t1 = -a @ (L * e) + (z[s] - v.ravel()[s]) / sigma ** 2
+            t2 = a @ (L * a) + 1.0 / sigma ** 2
+            d = -t1 / t2
+            z[s] += d
+            e -= a * d
+    return z
+
+
+def test_grouped_icd_with_single_voxel_groups_is_sequential_icd(oracle):
+    sc, y, lam = _tiny_problem(oracle, seed=6)
+    ang = sc.angles()[0]
+    shape = (4, 4, 4)
+    A = _dense_A(oracle, sc, ang, shape)
+    sigma = 0.4
+    v, z0 = synth.normal(7, shape), synth.normal(8, shape)
+    order = list(np.random.default_rng(9).permutation(64))
+    groups = []
+    for s_ in order:
+        m = np.zeros(64, bool); m[s_] = True
+        groups.append(m.reshape(shape))
+    got = oracle.prox_data_icd_frame(y[0], lam[0], v, z0, sc, ang, sigma, 2, groups)
+    ref = _icd_sequential(A, lam[0], y[0], v, z0, sigma, order, 2)
+    np.testing.assert_allclose(got.ravel(), ref, rtol=1e-10, atol=1e-12)
+
+
+def test_grouped_icd_descends_and_converges_to_dense_solve(oracle):
+    # parity groups: the cost of Eq. (4) never increases from sweep to sweep and
+    # the iterates reach the exact proximal map
+    sc, y, lam = _tiny_problem(oracle, seed=10)
+    ang = sc.angles()[0]
+    shape = (4, 4, 4)
+    A = _dense_A(oracle, sc, ang, shape)
+    sigma = 0.5
+    v = synth.normal(11, shape)
+    H = A.T @ (lam[0].ravel()[:, None] * A) + np.eye(64) / sigma ** 2
+    exact = np.linalg.solve(H, A.T @ (lam[0].ravel() * y[0].ravel()) + v.ravel() / sigma ** 2)
+    z = np.zeros(shape)
+    prev = oracle.data_cost(y[0], lam[0], v, z, sc, ang, sigma)
+    for _ in range(40):
+        z = oracle.prox_data_icd_frame(y[0], lam[0], v, z, sc, ang, sigma, 1)
+        c = oracle.data_cost(y[0], lam[0], v, z, sc, ang, sigma)
+        assert c <= prev * (1 + 1e-12)
+        prev = c
+    z = oracle.prox_data_icd_frame(y[0], lam[0], v, z, sc, ang, sigma, 400)
+    np.testing.assert_allclose(z.ravel(), exact, rtol=1e-7, atol=1e-9)
+
+
+def test_parity_groups_partition_the_volume(oracle):
+    g = oracle.parity_groups((3, 5, 4))
+    assert len(g) == 8
+    total = np.sum(g, axis=0)
+    assert np.all(total == 1)
+    # no two voxels of one group are neighbours along any axis
+    for m in g:
+        for ax in range(3):
+            assert not np.any(m & np.roll(m, 1, axis=ax)[...] & (np.indices(m.shape)[ax] > 0))
+
+
 def _gmrf_Q(shape4, sx, bt):
     # Hessian of h(z) = sum_{pairs} b rho(z_s - z_r) with p = q = 2, where
     # rho(D) = D^2/(4 sx^2): each pair adds b/(2 sx^2) [[1,-1],[-1,1]].
@@ -227,3 +304,89 @@ def test_consensus_residual_closed_forms(oracle):
     # Xbar = 1/4, deviations 3/4 and 1/4, r = sqrt(1/4 * 9/16 + 3/4 * 1/16) / (1/4) = sqrt(3)
     r2 = oracle.consensus_residual([np.ones(1), np.zeros(1)], mu)
     assert r2 == pytest.approx(math.sqrt(3.0), rel=1e-14)
+
+
+# ---------------------------------------------------------------- direct MAP (MBIR + 4D-MRF, Sec. VI)
+
+
+def _dense_system(oracle, sc, y, lam, n, nt):
+    ang = sc.angles()
+    N3 = n ** 3
+    H = np.zeros((nt * N3, nt * N3))
+    b = np.zeros(nt * N3)
+    for t in range(nt):
+        A = _dense_A(oracle, sc, ang[t], (n, n, n))
+        H[t * N3:(t + 1) * N3, t * N3:(t + 1) * N3] = A.T @ (lam[t].ravel()[:, None] * A)
+        b[t * N3:(t + 1) * N3] = A.T @ (lam[t].ravel() * y[t].ravel())
+    return H, b
+
+
+def test_map_quadratic_prior_equals_dense_solve(oracle):
+    # p = q = 2: the surrogate equals the prior, so one outer iteration with as
+    # many CG steps as unknowns solves (A^T Lambda A + beta Q) x = A^T Lambda y
+    n, nt = 4, 2
+    sc, y, lam = _tiny_problem(oracle, n=n, nt=nt, seed=12)
+    sx, bt, beta = 0.4, 0.5, 2.0
+    H, b = _dense_system(oracle, sc, y, lam, n, nt)
+    exact = np.linalg.solve(H + beta * _gmrf_Q((nt, n, n, n), sx, bt), b)
+    x = oracle.map_mm(y, lam, np.zeros((nt, n, n, n)), sc, 2.0, 2.0, 1.0, sx, bt, beta, 1, nt * n ** 3)
+    np.testing.assert_allclose(x.ravel(), exact, rtol=1e-8, atol=1e-10 * np.abs(exact).max())
+
+
+def test_surrogate_lap_is_half_the_surrogate_gradient(oracle):
+    # 2 L_a x is the gradient of Q(x) = sum_pairs b a(anchor) (x_s - x_r)^2, and
+    # at x = anchor it equals the gradient of h itself (the surrogate touches h
+    # there): both against central finite differences of the oracle's h
+    shape = (2, 3, 4, 3)
+    p, q, T, sx, bt = 2.0, 1.2, 1.0, 0.3, 0.5
+    anchor = synth.uniform(13, shape)
+    g = 2.0 * oracle.surrogate_lap(anchor, anchor, p, q, T, sx, bt)
+    fd = np.zeros(anchor.size)
+    h = 1e-6
+    for i in range(anchor.size):
+        e = np.zeros(anchor.size); e[i] = h
+        fd[i] = (oracle.qggmrf_cost(anchor + e.reshape(shape), p, q, T, sx, bt) -
+                 oracle.qggmrf_cost(anchor - e.reshape(shape), p, q, T, sx, bt)) / (2 * h)
+    np.testing.assert_allclose(g.ravel(), fd, rtol=1e-6, atol=1e-8)
+    # L_a is linear in x
+    x1, x2 = synth.normal(14, shape), synth.normal(15, shape)
+    np.testing.assert_allclose(oracle.surrogate_lap(anchor, 2 * x1 - x2, p, q, T, sx, bt),
+                               2 * oracle.surrogate_lap(anchor, x1, p, q, T, sx, bt)
+                               - oracle.surrogate_lap(anchor, x2, p, q, T, sx, bt), rtol=1e-12, atol=1e-12)
+
+
+def test_map_descends_and_reaches_a_stationary_point(oracle):
+    n, nt = 4, 2
+    sc, y, lam = _tiny_problem(oracle, n=n, nt=nt, seed=16)
+    p, q, T, sx, bt, beta = 2.0, 1.2, 1.0, 0.3, 0.5, 3.0
+    x = np.zeros((nt, n, n, n))
+    prev = oracle.map_cost(y, lam, x, sc, p, q, T, sx, bt, beta)
+    for _ in range(15):
+        x = oracle.map_mm(y, lam, x, sc, p, q, T, sx, bt, beta, 1, 4)
+        c = oracle.map_cost(y, lam, x, sc, p, q, T, sx, bt, beta)
+        assert c <= prev * (1 + 1e-12)
+        prev = c
+    x = oracle.map_mm(y, lam, x, sc, p, q, T, sx, bt, beta, 200, 30)
+    # gradient of Phi by central differences of the cost
+    fd = np.zeros(x.size)
+    h = 1e-6
+    for i in range(x.size):
+        e = np.zeros(x.size); e[i] = h
+        fd[i] = (oracle.map_cost(y, lam, x + e.reshape(x.shape), sc, p, q, T, sx, bt, beta) -
+                 oracle.map_cost(y, lam, x - e.reshape(x.shape), sc, p, q, T, sx, bt, beta)) / (2 * h)
+    H, b = _dense_system(oracle, sc, y, lam, n, nt)
+    assert np.linalg.norm(fd) <= 1e-6 * np.linalg.norm(b)
+
+
+def test_mace_with_exact_agents_reaches_the_map_point(oracle):
+    # Sec. III: with proximal agents the consensus equilibrium is the MAP point
+    # of l + (mu_1/mu_0) h; here the non-quadratic q-GGMRF prior (q = 1.2)
+    n, nt = 4, 2
+    sc, y, lam = _tiny_problem(oracle, n=n, nt=nt, seed=17)
+    p, q, T, sx, bt = 2.0, 1.2, 1.0, 0.3, 0.5
+    mu, sigma = [0.25, 0.75], 0.5
+    agents = [lambda w, x: oracle.prox_data(y, lam, w, x, sc, sigma, 64),
+              lambda w, x: oracle.prox_qggmrf(w, x, sigma, p, q, T, sx, bt, 200)]
+    xhat, W, X, res = oracle.mace(np.zeros((nt, n, n, n)), agents, mu, 0.5, 200)
+    xmap = oracle.map_mm(y, lam, np.zeros((nt, n, n, n)), sc, p, q, T, sx, bt, mu[1] / mu[0], 300, 30)
+    np.testing.assert_allclose(oracle.average(X, mu), xmap, rtol=1e-6, atol=1e-8 * np.abs(xmap).max())
