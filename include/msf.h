@@ -173,8 +173,8 @@ msf_status msf_weights(const float* d_counts, float* d_y, float* d_lambda, size_
 
 typedef struct msf_dataprox msf_dataprox;
 
-/* Workspace for the data proximal map on the projector's problem size:
- * four 4D volumes, one sinogram and per-frame FP64 scalars. */
+/* Workspace for the data proximal maps (CG and ICD) on the projector's problem
+ * size: four 4D volumes, two sinograms and per-frame FP64 partial sums. */
 msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out);
 void msf_dataprox_destroy(msf_dataprox* d);
 
@@ -187,6 +187,26 @@ void msf_dataprox_destroy(msf_dataprox* d);
  * d_y, d_lambda: sinogram-shaped; d_v, d_x: 4D volumes.  sigma > 0, n_cg >= 0. */
 msf_status msf_prox_data(msf_dataprox* d, const float* d_y, const float* d_lambda,
                          const float* d_v, float* d_x, double sigma, int n_cg, void* stream);
+
+/* Partial-update data proximal map L~(v; x) of Sec. III, Eq. (13), by
+ * iterative coordinate descent (the paper's own choice for L~, "a few ICD
+ * iterations"), on the cost of Eq. (4) with l from Eq. (2):
+ *     1/2 ||y - A z||^2_Lambda + ||z - v||^2 / (2 sigma^2),
+ * one independent solve per time-point, warm-started from d_x and written back.
+ * The voxel order is grouped so that a GPU can update many voxels at once: a
+ * sweep visits the eight parity groups g = (pz*2 + py)*2 + px, (pz,py,px) =
+ * (z,y,x) mod 2, in increasing order.  Inside a group every voxel s takes its
+ * own coordinate Newton step against the same error sinogram e = y - A z,
+ *     delta_s = -theta1_s / theta2_s,
+ *     theta1_s = -(A^T Lambda e)_s + (z_s - v_s)/sigma^2,
+ *     theta2_s = (A^T Lambda A)_ss + 1/sigma^2,
+ * and the group moves by alpha_t * delta with alpha_t the exact minimiser of the
+ * cost of frame t along delta; then e is updated.  (With one voxel per group
+ * alpha = 1 and this is sequential ICD; with groups every step still lowers the
+ * cost.)  n_sweeps sweeps; vectors FP32, the group sums and alpha FP64.
+ * Same arguments and workspace as msf_prox_data; sigma > 0, n_sweeps >= 0. */
+msf_status msf_prox_data_icd(msf_dataprox* d, const float* d_y, const float* d_lambda,
+                             const float* d_v, float* d_x, double sigma, int n_sweeps, void* stream);
 
 /* ------------------------------------------------------------ q-GGMRF agent */
 
@@ -207,6 +227,35 @@ typedef struct {
  * d_v, d_x: 4D volumes [nt][nz][ny][nx]. */
 msf_status msf_prox_qggmrf(const msf_vol* vol, const msf_mrf* prm, const float* d_v, float* d_x,
                            double sigma, int n_sweeps, void* stream);
+
+/* ------------------------------------------------------------ direct MAP (MBIR + 4D-MRF) */
+
+/* The "MBIR + 4D-MRF" comparison of Sec. VI solved directly, without the MACE
+ * split: the MAP estimate of Eq. (3),
+ *     x* = argmin_x  l(x) + beta h(x),   l(x) = 1/2 sum_t ||y_t - A_t x_t||^2_Lambda,
+ * with h the 4D q-GGMRF prior of msf_prox_qggmrf.  (With proximal agents and
+ * weights mu = (mu_0, mu_1) the MACE equilibrium of Sec. III is this point with
+ * beta = mu_1 / mu_0.)  The workspace holds four 4D volumes and a sinogram. */
+typedef struct msf_map msf_map;
+msf_status msf_map_create(msf_projector* p, msf_map** out);
+void msf_map_destroy(msf_map* m);
+
+/* Majorise-minimise: each of n_outer outer iterations replaces h by its
+ * symmetric-bound quadratic surrogate built at the current x (equal to h there,
+ * above it elsewhere: weights a(x_s - x_r) = rho'/(2 D) on every neighbour
+ * pair) and takes n_cg conjugate-gradient steps, warm-started at x, on
+ *     (A^T Lambda A + 2 beta L_a) x = A^T Lambda y,
+ * (L_a x)_s = sum_r b_sr a_sr (x_s - x_r), over the whole 4D volume (the prior
+ * couples the time-points, so the CG scalars are global; FP64).  Every outer
+ * iteration lowers the cost.  d_x: warm start, overwritten.  beta > 0,
+ * prm as msf_prox_qggmrf (p = 2, 1 <= q <= 2).  A non-finite CG scalar is
+ * reported by the next msf_map_cost as MSF_ERR_NUMERIC. */
+msf_status msf_map_solve(msf_map* m, const msf_mrf* prm, double beta, const float* d_y, const float* d_lambda,
+                         float* d_x, int n_outer, int n_cg, void* stream);
+
+/* h_cost[0] = l(x) + beta h(x) of Eq. (3) at d_x (FP64 sums; synchronises). */
+msf_status msf_map_cost(msf_map* m, const msf_mrf* prm, double beta, const float* d_y, const float* d_lambda,
+                        const float* d_x, double* h_cost, void* stream);
 
 /* ------------------------------------------------------------ CNN agents */
 
@@ -304,6 +353,8 @@ typedef struct {
     int n_cg;         /* CG iterations of the partial update L~ (Eq. (13)) */
     int n_sweeps;     /* ICD sweeps of the q-GGMRF agent per iteration */
     int use_graph;    /* non-zero: run the iteration as a CUDA graph (see msf_mace_step) */
+    int n_icd;        /* > 0: the data agent runs n_icd grouped-ICD sweeps
+                         (msf_prox_data_icd) instead of n_cg CG iterations */
 } msf_mace_params;
 
 msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out);
@@ -312,7 +363,9 @@ void msf_mace_destroy(msf_mace* m);
 /* One pass of Algorithm 1:  X <- F~(W; X);  Z <- G(2X - W);  W <- W + 2 rho (Z - X).
  * X_0 <- L~(W_0; X_0) (warm-started CG), X_k <- H_k(W_k); the average of Eq. (9)
  * uses mu.  h_residual (optional, synchronises) receives the FP64 consensus
- * spread sqrt(sum_i mu_i ||X_i - Xbar||^2) / ||Xbar|| of the new X.
+ * spread sqrt(sum_i mu_i ||X_i - Xbar||^2) / ||Xbar|| of the new X; a
+ * non-finite CG or ICD scalar of the data agent in this or an earlier step is
+ * reported there as MSF_ERR_NUMERIC.
  * With the q-GGMRF prior the data agent and the prior agent run concurrently
  * on two internal streams forked from `stream` and joined before the
  * consensus (the CNN agents run in stream order); the step as a whole is

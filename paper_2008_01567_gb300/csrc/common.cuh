@@ -18,8 +18,13 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Checks the device is usable for the kernels of this library (sm_103).
 msf_status check_device();
 
-// The volume a projector plan was built for.
+// The volume a projector plan was built for, and its sinogram size (rays).
 const msf_vol* projector_volume(const msf_projector* p);
+size_t projector_sino_size(const msf_projector* p);
+
+// Device status word of a data-agent workspace: 0, or MSF_ERR_NUMERIC once a
+// CG or ICD scalar was non-finite (sticky).
+int* dataprox_status(msf_dataprox* d);
 
 // CNN handle state used by the MACE orchestration: a counter that changes with
 // the parameters, and the out-of-stream set-up done before a graph capture.

@@ -1,6 +1,6 @@
 // MACE consensus and the partial-update Mann iteration (Sec. III, Algorithm 1).
 //
-//   X <- F~(W; X)           (data agent L~ by warm-started CG, prior agents H_k)
+//   X <- F~(W; X)           (data agent L~ by warm-started CG or grouped ICD, prior agents H_k)
 //   Z <- G(2X - W)          (Eqs. (8)-(9): weighted average, replicated)
 //   W <- W + 2 rho (Z - X)
 //
@@ -22,6 +22,7 @@ struct msf_mace {
     double* d_partial = nullptr;   // [2][nblocks]
     double* d_sums = nullptr;      // [2]
     double* h_sums = nullptr;      // pinned [2], written by the step's last copy
+    int* h_status = nullptr;       // pinned copy of the data agent's numeric status word
     int nblocks = 0;
     size_t N = 0;                  // voxels of one 4D volume
     // with the q-GGMRF prior the data agent and the prior agent run on two
@@ -189,7 +190,8 @@ static msf_status check_params(const msf_mace* m, const msf_mace_params* prm) {
         musum += prm->mu[i];
     }
     MSF_REQUIRE(fabs(musum - 1.0) < 1e-9, "msf_mace_step: agent weights must sum to 1 (got %.17g)", musum);
-    MSF_REQUIRE(prm->n_cg >= 0 && prm->n_sweeps >= 0, "msf_mace_step: iteration counts must be >= 0");
+    MSF_REQUIRE(prm->n_cg >= 0 && prm->n_sweeps >= 0 && prm->n_icd >= 0,
+                "msf_mace_step: iteration counts must be >= 0");
     return MSF_OK;
 }
 
@@ -214,8 +216,11 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
     }
     void* sp = reinterpret_cast<void*>(fork ? m->s_prox : st);
     void* sa = reinterpret_cast<void*>(fork ? m->s_prior : st);
-    // X_0 <- L~(W_0; X_0)
-    MSF_TRY(msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, sp));
+    // X_0 <- L~(W_0; X_0): n_cg CG iterations, or n_icd grouped-ICD sweeps
+    if (prm->n_icd > 0)
+        MSF_TRY(msf_prox_data_icd(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_icd, sp));
+    else
+        MSF_TRY(msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, sp));
     // X_k <- H_k(W_k)
     for (int k = 1; k < K1; ++k) {
         if (d.prior == MSF_PRIOR_QGGMRF) {
@@ -238,10 +243,13 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
     c.K1 = K1;
     MSF_TRY(launch_consensus(d.d_W, d.d_X, K1, N, c, m->d_partial, m->d_sums, st));
     MSF_TRY_CUDA(cudaMemcpyAsync(m->h_sums, m->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MSF_TRY_CUDA(cudaMemcpyAsync(m->h_status, dataprox_status(m->dp), sizeof(int), cudaMemcpyDeviceToHost, st));
     return MSF_OK;
 }
 
 static msf_status read_residual(const msf_mace* m, double* h_residual) {
+    if (*m->h_status != 0)
+        return fail(MSF_ERR_NUMERIC, "msf_mace_step: non-finite CG or ICD scalar in the data agent");
     const double num = m->h_sums[0], den = m->h_sums[1];
     if (!isfinite(num) || !isfinite(den)) return fail(MSF_ERR_NUMERIC, "msf_mace_step: non-finite consensus residual");
     *h_residual = den > 0 ? sqrt(num / den) : sqrt(num);
@@ -250,7 +258,7 @@ static msf_status read_residual(const msf_mace* m, double* h_residual) {
 
 static bool same_params(const msf_mace_params& a, const msf_mace_params& b) {
     return a.rho == b.rho && a.sigma == b.sigma && memcmp(a.mu, b.mu, sizeof(a.mu)) == 0 && a.n_cg == b.n_cg &&
-           a.n_sweeps == b.n_sweeps;
+           a.n_sweeps == b.n_sweeps && a.n_icd == b.n_icd;
 }
 
 static void drop_graph(cudaGraphExec_t& g) {
@@ -337,6 +345,7 @@ extern "C" msf_status msf_mace_create(const msf_mace_desc* desc, msf_mace** out)
     if (cudaMalloc(&m->d_partial, 2 * m->nblocks * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->d_sums, 2 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&m->h_sums, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&m->h_status, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
         !make_agent_streams(m)) {
         cudaGetLastError();
@@ -360,6 +369,7 @@ extern "C" void msf_mace_destroy(msf_mace* m) {
     cudaFree(m->d_partial);
     cudaFree(m->d_sums);
     if (m->h_sums) cudaFreeHost(m->h_sums);
+    if (m->h_status) cudaFreeHost(m->h_status);
     delete m;
 }
 

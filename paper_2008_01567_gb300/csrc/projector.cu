@@ -539,6 +539,261 @@ __global__ void cg_update_kernel(float* __restrict__ z, float* __restrict__ r,
     if (threadIdx.x == 0) partial[(size_t)t * gridDim.x + blockIdx.x] = s;
 }
 
+// ------------------------------------------------------------------ grouped ICD data agent
+//
+// The partial update L~ of Sec. III as coordinate descent on the cost of
+// Eq. (4).  A sweep visits the eight parity groups (pz*2 + py)*2 + px of the
+// voxels in increasing order; inside a group every voxel takes its own Newton
+// step against the same step-weighted residual sinogram e' = step*Lambda*(y - Az),
+//     delta_s = -theta1_s / theta2_s,
+//     theta1_s = -(A^T Lambda e)_s + (z_s - v_s)/sigma^2,
+//     theta2_s = sum_r Lambda_r a_rs^2 + 1/sigma^2,
+// and the group moves by alpha_t delta (per frame t), alpha_t the exact
+// minimiser of the quadratic cost along delta.  A parity group holds at most
+// one of the four bilinear taps of any ray-plane crossing.
+
+constexpr int ICD_SINO_BLOCKS = 256;   // blocks per frame of the sinogram passes
+constexpr int ICD_ZB = 8;              // group voxels per z-run of the group gather (16 slices)
+
+// Adds, for the rays of one view whose major axis is XMAJ, the gather terms of
+// the voxels (ix, iy, base + ZS*j), j < ZB, into acc[j]: w_a w_z e' (SQ false)
+// or w_a^2 w_z^2 e' (SQ true, with e' = step^2 Lambda: the diagonal of
+// A^T Lambda A).  Candidate columns, the a weight and the affine z crossing per
+// row are formed exactly as in gather_runs.
+template <bool XMAJ, int ZB, int ZS, bool SQ>
+__device__ __forceinline__ void gather_icd(const float4* __restrict__ col, const float* __restrict__ e, int g,
+                                           int ix, int iy, int base, float cs, float sn, const ProjDims& d,
+                                           float (*acc)[128], int tid) {
+    const int kpl = XMAJ ? ix : iy;
+    const int ia = XMAJ ? iy : ix;
+    const float cmaj = XMAJ ? d.cx : d.cy;
+    const float xc = (ix - d.cx) * d.vox, yc = (iy - d.cy) * d.vox;
+    float u1, u2;
+    if (XMAJ) {
+        u1 = u_pixel(xc, yc - d.vox, cs, sn, d);
+        u2 = u_pixel(xc, yc + d.vox, cs, sn, d);
+    } else {
+        u1 = u_pixel(xc - d.vox, yc, cs, sn, d);
+        u2 = u_pixel(xc + d.vox, yc, cs, sn, d);
+    }
+    const int iu_lo = max(0, (int)floorf(fminf(u1, u2)) - 1);
+    const int iu_hi = min(d.nu - 1, (int)ceilf(fmaxf(u1, u2)) + 1);
+    const float tk = __fsub_rn((float)kpl, cmaj);
+    const float inv_dv = 1.0f / d.dv;
+    const int zlast = base + ZS * (ZB - 1);
+    for (int iu = iu_lo; iu <= iu_hi; ++iu) {
+        const ColParams c = load_col(col, (size_t)g * d.nu + iu);
+        if ((c.xmajor != 0.0f) != XMAJ) continue;
+        const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
+        const float a0f = floorf(fa);
+        const int a0 = (int)a0f;
+        if (ia != a0 && ia != a0 + 1) continue;
+        const float wa1 = __fsub_rn(fa, a0f);
+        const float wa = (ia == a0) ? __fsub_rn(1.0f, wa1) : wa1;
+        const float wav = SQ ? __fmul_rn(wa, wa) : wa;
+        const float rgz = __fdividef(1.0f, c.c1 + tk * c.inv_dmaj);
+        const float va = (base - 1 - d.cz) * rgz * inv_dv + d.cv;
+        const float vb = (zlast + 1 - d.cz) * rgz * inv_dv + d.cv;
+        const int iv_lo = max(0, (int)floorf(va) - 1);
+        const int iv_hi = min(d.nv - 1, (int)ceilf(vb) + 1);
+        const float* erow = e + ((size_t)g * d.nv) * d.nu + iu;
+        const RayZ rzb = ray_z(c, det_v(0, d), d.cz);
+        const float fzb = __fmaf_rn(tk, rzb.bz, rzb.fz_mid);
+        const float dfz = d.dv * __fmaf_rn(tk, c.inv_dmaj, c.c1);
+        for (int iv = iv_lo; iv <= iv_hi; ++iv) {
+            const float fz = __fmaf_rn((float)iv, dfz, fzb);
+            const float z0f = floorf(fz);
+            const int z0 = (int)z0f;
+            if (z0 + 1 < base || z0 > zlast) continue;
+            const float ev = __fmul_rn(wav, __ldg(erow + (size_t)iv * d.nu));
+            const float wz1 = __fsub_rn(fz, z0f);
+            const float w1 = SQ ? __fmul_rn(wz1, wz1) : wz1;
+            const float w0 = SQ ? __fmul_rn(__fsub_rn(1.0f, wz1), __fsub_rn(1.0f, wz1)) : 0.0f;
+            const float c1 = __fmul_rn(w1, ev);
+            const float c0 = SQ ? __fmul_rn(w0, ev) : __fsub_rn(ev, c1);
+            const int o0 = z0 - base, o1 = z0 + 1 - base;
+            if (o0 >= 0 && o0 % ZS == 0 && o0 / ZS < ZB) acc[o0 / ZS][tid] = __fadd_rn(acc[o0 / ZS][tid], c0);
+            if (o1 >= 0 && o1 % ZS == 0 && o1 / ZS < ZB) acc[o1 / ZS][tid] = __fadd_rn(acc[o1 / ZS][tid], c1);
+        }
+    }
+}
+
+// theta2 = (A^T Lambda A)_ss + 1/sigma^2 for every voxel: the squared-weight
+// gather of e2 = step^2 Lambda.  Grid and runs as joseph_adj_kernel.
+template <int ZB>
+__global__ void __launch_bounds__(128) icd_theta2_kernel(const float4* __restrict__ col,
+                                                         const float2* __restrict__ trig,
+                                                         const int* __restrict__ vflag,
+                                                         const float* __restrict__ e2, float* __restrict__ theta2,
+                                                         float inv_s2, ProjDims d) {
+    __shared__ float acc[ZB][128];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int ix = blockIdx.x * 32 + threadIdx.x;
+    const int iy = blockIdx.y * 4 + threadIdx.y;
+    const int nzb = (d.nz + ZB - 1) / ZB;
+    const int zb = blockIdx.z % nzb, t = blockIdx.z / nzb;
+    const int base = zb * ZB;
+    const bool inside = ix < d.nx && iy < d.ny;
+#pragma unroll
+    for (int k = 0; k < ZB; ++k) acc[k][tid] = 0.0f;
+    if (inside) {
+        for (int j = 0; j < d.views; ++j) {
+            const int g = t * d.views + j;
+            const float2 cs = __ldg(trig + g);
+            const int fl = __ldg(vflag + g);
+            if (fl & 1) gather_icd<true, ZB, 1, true>(col, e2, g, ix, iy, base, cs.x, cs.y, d, acc, tid);
+            if (fl & 2) gather_icd<false, ZB, 1, true>(col, e2, g, ix, iy, base, cs.x, cs.y, d, acc, tid);
+        }
+        for (int k = 0; k < ZB && base + k < d.nz; ++k)
+            theta2[(((size_t)t * d.nz + base + k) * d.ny + iy) * d.nx + ix] = acc[k][tid] + inv_s2;
+    }
+}
+
+// Group dimensions: voxels of parity p along an axis of n voxels.
+__host__ __device__ __forceinline__ int par_count(int n, int p) { return (n - p + 1) / 2; }
+
+struct IcdGroup {
+    int px, py, pz;
+    int gx, gy, gz;   // group voxels along x, y, z
+    int nzb;          // z-runs of ZB group voxels per column
+};
+
+// The group step's gather: for every voxel s of the group, delta_s =
+// -theta1_s/theta2_s (written to dlt), and per-block partial sums of
+// theta1.delta and delta.delta (FP64, fixed order).  A thread owns one group
+// column (ix, iy) and a run of ZB group voxels along z (stride 2).
+template <int ZB>
+__global__ void __launch_bounds__(128) icd_group_kernel(const float4* __restrict__ col,
+                                                        const float2* __restrict__ trig,
+                                                        const int* __restrict__ vflag, const float* __restrict__ e,
+                                                        const float* __restrict__ z, const float* __restrict__ v,
+                                                        const float* __restrict__ theta2, float* __restrict__ dlt,
+                                                        double* __restrict__ partial, float inv_s2, IcdGroup G,
+                                                        ProjDims d) {
+    __shared__ float acc[ZB][128];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int jx = blockIdx.x * 32 + threadIdx.x, jy = blockIdx.y * 4 + threadIdx.y;
+    const int ix = 2 * jx + G.px, iy = 2 * jy + G.py;
+    const int zb = blockIdx.z % G.nzb, t = blockIdx.z / G.nzb;
+    const int base = G.pz + 2 * ZB * zb;
+    const bool inside = jx < G.gx && jy < G.gy;
+#pragma unroll
+    for (int k = 0; k < ZB; ++k) acc[k][tid] = 0.0f;
+    if (inside) {
+        for (int j = 0; j < d.views; ++j) {
+            const int g = t * d.views + j;
+            const float2 cs = __ldg(trig + g);
+            const int fl = __ldg(vflag + g);
+            if (fl & 1) gather_icd<true, ZB, 2, false>(col, e, g, ix, iy, base, cs.x, cs.y, d, acc, tid);
+            if (fl & 2) gather_icd<false, ZB, 2, false>(col, e, g, ix, iy, base, cs.x, cs.y, d, acc, tid);
+        }
+    }
+    double gd = 0.0, dd = 0.0;
+    for (int k = 0; k < ZB; ++k) {
+        const int iz = base + 2 * k;
+        if (!inside || iz >= d.nz) break;
+        const size_t i = (((size_t)t * d.nz + iz) * d.ny + iy) * d.nx + ix;
+        const float th1 = __fmaf_rn(__fsub_rn(z[i], v[i]), inv_s2, -acc[k][tid]);
+        const float del = -__fdiv_rn(th1, theta2[i]);
+        dlt[i] = del;
+        gd += (double)th1 * (double)del;
+        dd += (double)del * (double)del;
+    }
+    const double sg = block_sum_f64(gd);
+    const double sd = block_sum_f64(dd);
+    if (tid == 0) {
+        const int bpf = gridDim.x * gridDim.y * G.nzb;
+        const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zb);
+        partial[2 * ((size_t)t * bpf + b)] = sg;
+        partial[2 * ((size_t)t * bpf + b) + 1] = sd;
+    }
+}
+
+// Sinogram passes of a group step, per frame (grid ICD_SINO_BLOCKS x nt):
+//   PASS 0: per-block partial sums of Lambda (A delta)^2
+//   PASS 1: e' -= alpha_t step Lambda (A delta)
+// ad = A delta (plain forward), lam = Lambda, e' the step-weighted residual.
+template <int PASS>
+__global__ void __launch_bounds__(256) icd_sino_kernel(const float4* __restrict__ col,
+                                                       const float* __restrict__ ad, const float* __restrict__ lam,
+                                                       float* __restrict__ e, const double* __restrict__ alpha,
+                                                       double* __restrict__ partial, ProjDims d) {
+    const int t = blockIdx.y;
+    const size_t per_view = (size_t)d.nu * d.nv, mt = per_view * d.views;
+    const size_t off = (size_t)t * mt;
+    const float a = PASS == 1 ? (float)alpha[t] : 0.0f;
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < mt; i += (size_t)gridDim.x * blockDim.x) {
+        const float val = ad[off + i];
+        const float l = lam[off + i];
+        if (PASS == 0) {
+            s += (double)l * (double)val * (double)val;
+        } else {
+            const int j = (int)(i / per_view);
+            const int iv = (int)((i % per_view) / d.nu), iu = (int)(i % d.nu);
+            const ColParams c = load_col(col, ((size_t)t * d.views + j) * d.nu + iu);
+            const float step = ray_z(c, det_v(iv, d), d.cz).step;
+            e[off + i] = __fmaf_rn(-a, __fmul_rn(step, __fmul_rn(l, val)), e[off + i]);
+        }
+    }
+    if (PASS == 0) {
+        const double b = block_sum_f64(s);
+        if (threadIdx.x == 0) partial[(size_t)t * gridDim.x + blockIdx.x] = b;
+    }
+}
+
+// alpha_t = -sum(theta1.delta) / (sum Lambda (A delta)^2 + sum(delta.delta)/sigma^2)
+// per frame (one block each), from the partials of the group gather (bpf per
+// frame) and of sinogram pass 0, summed in a fixed order.
+__global__ void icd_alpha_kernel(const double* __restrict__ gpart, int bpf, const double* __restrict__ spart,
+                                 double inv_s2, double* __restrict__ alpha, int* __restrict__ status) {
+    const int t = blockIdx.x;
+    double gd = 0.0, dd = 0.0, sq = 0.0;
+    for (int i = threadIdx.x; i < bpf; i += blockDim.x) {
+        gd += gpart[2 * ((size_t)t * bpf + i)];
+        dd += gpart[2 * ((size_t)t * bpf + i) + 1];
+    }
+    for (int i = threadIdx.x; i < ICD_SINO_BLOCKS; i += blockDim.x) sq += spart[(size_t)t * ICD_SINO_BLOCKS + i];
+    gd = block_sum_f64(gd);
+    dd = block_sum_f64(dd);
+    sq = block_sum_f64(sq);
+    if (threadIdx.x == 0) {
+        const double den = sq + dd * inv_s2;
+        if (!isfinite(gd) || !isfinite(den)) atomicExch(status, (int)MSF_ERR_NUMERIC);
+        alpha[t] = (den > 0.0 && isfinite(den) && isfinite(gd)) ? -gd / den : 0.0;
+    }
+}
+
+// z_s += alpha_t delta_s and delta_s = 0 for the voxels of the group.
+__global__ void icd_update_kernel(float* __restrict__ z, float* __restrict__ dlt, const double* __restrict__ alpha,
+                                  IcdGroup G, ProjDims d) {
+    const size_t per_frame = (size_t)G.gx * G.gy * G.gz;
+    const size_t total = per_frame * d.nt;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int t = (int)(i / per_frame);
+        size_t r = i % per_frame;
+        const int jz = (int)(r / ((size_t)G.gx * G.gy));
+        r %= (size_t)G.gx * G.gy;
+        const int jy = (int)(r / G.gx), jx = (int)(r % G.gx);
+        const size_t k = (((size_t)t * d.nz + 2 * jz + G.pz) * d.ny + 2 * jy + G.py) * d.nx + 2 * jx + G.px;
+        z[k] = __fmaf_rn((float)alpha[t], dlt[k], z[k]);
+        dlt[k] = 0.0f;
+    }
+}
+
+// e2 = step^2 Lambda for every ray (input of the theta2 gather).
+__global__ void icd_step2_kernel(const float4* __restrict__ col, const float* __restrict__ lam,
+                                 float* __restrict__ out, ProjDims d) {
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * 4 + threadIdx.y;
+    const int g = blockIdx.z;
+    if (iu >= d.nu || iv >= d.nv) return;
+    const ColParams c = load_col(col, (size_t)g * d.nu + iu);
+    const float step = ray_z(c, det_v(iv, d), d.cz).step;
+    const size_t ray = ((size_t)g * d.nv + iv) * d.nu + iu;
+    out[ray] = __fmul_rn(__fmul_rn(step, step), lam[ray]);
+}
+
 // ------------------------------------------------------------------ phantom (test data)
 
 #define MSF_MAX_ELL_RECORDS 256
@@ -641,6 +896,11 @@ struct msf_dataprox {
     double *d_partial = nullptr, *d_rr = nullptr, *d_alpha = nullptr, *d_beta = nullptr;
     int* d_status = nullptr;
     int parts_adj = 0, parts_upd = 0, parts_max = 0;
+    // grouped ICD: a second sinogram (A delta, and step^2 Lambda for theta2),
+    // the group gather's partial sums and the sinogram pass's partial sums
+    float* d_s2 = nullptr;
+    double *d_ipart = nullptr, *d_spart = nullptr;
+    int parts_icd = 0;
 };
 
 namespace msf {
@@ -723,6 +983,8 @@ static msf_status launch_adj(msf_projector* p, int mode, const float* e, float* 
 using namespace msf;
 
 const msf_vol* msf::projector_volume(const msf_projector* p) { return &p->vol; }
+int* msf::dataprox_status(msf_dataprox* d) { return d->d_status; }
+size_t msf::projector_sino_size(const msf_projector* p) { return sino_size(p); }
 
 extern "C" msf_status msf_projector_create(const msf_geom* geom, const msf_vol* vol,
                                            msf_projector** out) {
@@ -838,7 +1100,15 @@ extern "C" msf_status msf_dataprox_create(msf_projector* p, msf_dataprox** out) 
     d->parts_upd = 512;
     d->parts_max = d->parts_adj > d->parts_upd ? d->parts_adj : d->parts_upd;
     const int nt = p->vol.nt;
-    if (cudaMalloc(&d->d_r, nv * 4) != cudaSuccess || cudaMalloc(&d->d_p, nv * 4) != cudaSuccess ||
+    {   // the largest group grid (parity 0 along every axis)
+        const msf_vol& v = p->vol;
+        d->parts_icd = ((par_count(v.nx, 0) + 31) / 32) * ((par_count(v.ny, 0) + 3) / 4) *
+                       ((par_count(v.nz, 0) + ICD_ZB - 1) / ICD_ZB);
+    }
+    if (cudaMalloc(&d->d_s2, ns * 4) != cudaSuccess ||
+        cudaMalloc(&d->d_ipart, (size_t)nt * d->parts_icd * 2 * 8) != cudaSuccess ||
+        cudaMalloc(&d->d_spart, (size_t)nt * ICD_SINO_BLOCKS * 8) != cudaSuccess ||
+        cudaMalloc(&d->d_r, nv * 4) != cudaSuccess || cudaMalloc(&d->d_p, nv * 4) != cudaSuccess ||
         cudaMalloc(&d->d_p2, nv * 4) != cudaSuccess ||
         cudaMalloc(&d->d_q, nv * 4) != cudaSuccess || cudaMalloc(&d->d_s, ns * 4) != cudaSuccess ||
         cudaMalloc(&d->d_partial, (size_t)nt * d->parts_max * 8) != cudaSuccess ||
@@ -861,6 +1131,7 @@ extern "C" void msf_dataprox_destroy(msf_dataprox* d) {
     cudaFree(d->d_r); cudaFree(d->d_p); cudaFree(d->d_p2); cudaFree(d->d_q); cudaFree(d->d_s);
     cudaFree(d->d_partial); cudaFree(d->d_rr); cudaFree(d->d_alpha); cudaFree(d->d_beta);
     cudaFree(d->d_status);
+    cudaFree(d->d_s2); cudaFree(d->d_ipart); cudaFree(d->d_spart);
     delete d;
 }
 
@@ -924,6 +1195,79 @@ extern "C" msf_status msf_prox_data(msf_dataprox* dp, const float* d_y, const fl
             MSF_PROF("cg_finalize", st);
             cg_finalize_kernel<FIN_BETA><<<nt, 256, 0, st>>>(dp->d_partial, dp->parts_upd, dp->d_rr, dp->d_beta, dp->d_status);
             MSF_LAUNCH_CHECK();
+        }
+    }
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_prox_data_icd(msf_dataprox* dp, const float* d_y, const float* d_lambda,
+                                        const float* d_v, float* d_x, double sigma, int n_sweeps, void* stream) {
+    MSF_REQUIRE(dp && d_y && d_lambda && d_v && d_x, "msf_prox_data_icd: NULL argument");
+    MSF_REQUIRE(sigma > 0 && isfinite(sigma), "msf_prox_data_icd: sigma must be positive");
+    MSF_REQUIRE(n_sweeps >= 0, "msf_prox_data_icd: n_sweeps must be >= 0");
+    if (n_sweeps == 0) return MSF_OK;
+    msf_projector* p = dp->p;
+    cudaStream_t st = as_stream(stream);
+    const ProjDims& d = p->dims;
+    const msf_vol& v = p->vol;
+    const int nt = v.nt;
+    const float inv_s2 = (float)(1.0 / (sigma * sigma));
+    // e' = step Lambda (y - A z)
+    MSF_TRY(launch_fwd(p, FWD_RESIDUAL, d_x, dp->d_s, d_lambda, d_y, st));
+    {   // theta2 = (A^T Lambda A)_ss + 1/sigma^2
+        MSF_PROF("icd_step2", st);
+        icd_step2_kernel<<<dim3((d.nu + 31) / 32, (d.nv + 3) / 4, d.nt * d.views), dim3(32, 4), 0, st>>>(
+            p->d_col, d_lambda, dp->d_s2, d);
+        MSF_LAUNCH_CHECK();
+    }
+    {
+        MSF_PROF("icd_theta2", st);
+        const dim3 grid((d.nx + 31) / 32, (d.ny + 3) / 4, ((d.nz + 15) / 16) * d.nt);
+        icd_theta2_kernel<16><<<grid, dim3(32, 4), 0, st>>>(p->d_col, p->d_trig, p->d_vflag, dp->d_s2, dp->d_q,
+                                                            inv_s2, d);
+        MSF_LAUNCH_CHECK();
+    }
+    MSF_TRY_CUDA(cudaMemsetAsync(dp->d_p, 0, vol_size(v) * sizeof(float), st));
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        for (int grp = 0; grp < 8; ++grp) {
+            IcdGroup G;
+            G.px = grp & 1; G.py = (grp >> 1) & 1; G.pz = grp >> 2;
+            G.gx = par_count(v.nx, G.px); G.gy = par_count(v.ny, G.py); G.gz = par_count(v.nz, G.pz);
+            if (G.gx == 0 || G.gy == 0 || G.gz == 0) continue;
+            G.nzb = (G.gz + ICD_ZB - 1) / ICD_ZB;
+            const dim3 grid((G.gx + 31) / 32, (G.gy + 3) / 4, G.nzb * nt);
+            const int bpf = grid.x * grid.y * G.nzb;
+            {
+                MSF_PROF("icd_group", st);
+                icd_group_kernel<ICD_ZB><<<grid, dim3(32, 4), 0, st>>>(p->d_col, p->d_trig, p->d_vflag, dp->d_s,
+                                                                      d_x, d_v, dp->d_q, dp->d_p, dp->d_ipart,
+                                                                      inv_s2, G, d);
+                MSF_LAUNCH_CHECK();
+            }
+            MSF_TRY(launch_fwd(p, FWD_PLAIN, dp->d_p, dp->d_s2, nullptr, nullptr, st));   // A delta
+            {
+                MSF_PROF("icd_sino", st);
+                icd_sino_kernel<0><<<dim3(ICD_SINO_BLOCKS, nt), 256, 0, st>>>(p->d_col, dp->d_s2, d_lambda, dp->d_s,
+                                                                              nullptr, dp->d_spart, d);
+                MSF_LAUNCH_CHECK();
+            }
+            {
+                MSF_PROF("icd_alpha", st);
+                icd_alpha_kernel<<<nt, 256, 0, st>>>(dp->d_ipart, bpf, dp->d_spart, 1.0 / (sigma * sigma), dp->d_alpha,
+                                                     dp->d_status);
+                MSF_LAUNCH_CHECK();
+            }
+            {
+                MSF_PROF("icd_update", st);
+                icd_update_kernel<<<152 * 4, 256, 0, st>>>(d_x, dp->d_p, dp->d_alpha, G, d);
+                MSF_LAUNCH_CHECK();
+            }
+            {
+                MSF_PROF("icd_sino", st);
+                icd_sino_kernel<1><<<dim3(ICD_SINO_BLOCKS, nt), 256, 0, st>>>(p->d_col, dp->d_s2, d_lambda, dp->d_s,
+                                                                              dp->d_alpha, nullptr, d);
+                MSF_LAUNCH_CHECK();
+            }
         }
     }
     return MSF_OK;

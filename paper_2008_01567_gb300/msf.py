@@ -54,7 +54,8 @@ class msf_mace_desc(ctypes.Structure):
 
 class msf_mace_params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("sigma", ctypes.c_double), ("mu", ctypes.c_double * 4),
-                ("n_cg", ctypes.c_int), ("n_sweeps", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("n_cg", ctypes.c_int), ("n_sweeps", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("n_icd", ctypes.c_int)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -76,6 +77,11 @@ _SIGS = {
     "msf_dataprox_create": (_I, [_P, ctypes.POINTER(_P)]),
     "msf_dataprox_destroy": (None, [_P]),
     "msf_prox_data": (_I, [_P, _P, _P, _P, _P, _D, _I, _P]),
+    "msf_prox_data_icd": (_I, [_P, _P, _P, _P, _P, _D, _I, _P]),
+    "msf_map_create": (_I, [_P, ctypes.POINTER(_P)]),
+    "msf_map_destroy": (None, [_P]),
+    "msf_map_solve": (_I, [_P, ctypes.POINTER(msf_mrf), _D, _P, _P, _P, _I, _I, _P]),
+    "msf_map_cost": (_I, [_P, ctypes.POINTER(msf_mrf), _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "msf_prox_qggmrf": (_I, [ctypes.POINTER(msf_vol), ctypes.POINTER(msf_mrf), _P, _P, _D, _I, _P]),
     "msf_cnn_create": (_I, [ctypes.c_int64, ctypes.POINTER(_P)]),
     "msf_cnn_destroy": (None, [_P]),
@@ -240,9 +246,46 @@ def msf_prox_data(dp: DataProx, y, lam, v, x, sigma: float, n_cg: int, stream=No
     _check(lib().msf_prox_data(dp.handle, _f32(y), _f32(lam), _f32(v), _f32(x), sigma, n_cg, _stream(stream)))
 
 
+def msf_prox_data_icd(dp: DataProx, y, lam, v, x, sigma: float, n_sweeps: int, stream=None):
+    _check(lib().msf_prox_data_icd(dp.handle, _f32(y), _f32(lam), _f32(v), _f32(x), sigma, n_sweeps,
+                                   _stream(stream)))
+
+
 def msf_prox_qggmrf(vol: msf_vol, mrf: msf_mrf, v, x, sigma: float, n_sweeps: int, stream=None):
     _check(lib().msf_prox_qggmrf(ctypes.byref(vol), ctypes.byref(mrf), _f32(v), _f32(x), sigma, n_sweeps,
                                  _stream(stream)))
+
+
+# ------------------------------------------------------------------ direct MAP
+
+
+class MapSolver:
+    """Owns an msf_map workspace for a projector's problem size."""
+
+    def __init__(self, proj: Projector):
+        h = ctypes.c_void_p()
+        _check(lib().msf_map_create(proj.handle, ctypes.byref(h)))
+        self.handle = h
+        self.proj = proj
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().msf_map_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def msf_map_solve(ms: MapSolver, mrf: msf_mrf, beta: float, y, lam, x, n_outer: int, n_cg: int, stream=None):
+    _check(lib().msf_map_solve(ms.handle, ctypes.byref(mrf), beta, _f32(y), _f32(lam), _f32(x), n_outer, n_cg,
+                               _stream(stream)))
+
+
+def msf_map_cost(ms: MapSolver, mrf: msf_mrf, beta: float, y, lam, x, stream=None) -> float:
+    c = ctypes.c_double(0.0)
+    _check(lib().msf_map_cost(ms.handle, ctypes.byref(mrf), beta, _f32(y), _f32(lam), _f32(x), ctypes.byref(c),
+                              _stream(stream)))
+    return c.value
 
 
 # ------------------------------------------------------------------ CNN
@@ -362,14 +405,15 @@ class Mace:
     __del__ = close
 
 
-def mace_params(rho: float, sigma: float, mu, n_cg: int, n_sweeps: int = 0, use_graph: bool = False):
+def mace_params(rho: float, sigma: float, mu, n_cg: int, n_sweeps: int = 0, use_graph: bool = False,
+                n_icd: int = 0):
     return msf_mace_params(rho, sigma, (ctypes.c_double * 4)(*(list(mu) + [0.0] * (4 - len(mu)))), n_cg, n_sweeps,
-                           1 if use_graph else 0)
+                           1 if use_graph else 0, n_icd)
 
 
 def msf_mace_step(m: Mace, rho: float, sigma: float, mu, n_cg: int, n_sweeps: int = 0, stream=None,
-                  want_residual: bool = True, use_graph: bool = False):
-    prm = mace_params(rho, sigma, mu, n_cg, n_sweeps, use_graph)
+                  want_residual: bool = True, use_graph: bool = False, n_icd: int = 0):
+    prm = mace_params(rho, sigma, mu, n_cg, n_sweeps, use_graph, n_icd)
     r = ctypes.c_double(0.0)
     _check(lib().msf_mace_step(m.handle, ctypes.byref(prm), ctypes.byref(r) if want_residual else None,
                                _stream(stream)))
