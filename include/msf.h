@@ -307,6 +307,26 @@ msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels);
  * msf_cnn_get_params; the running-statistics entries are zero). */
 msf_status msf_cnn_get_grads(msf_cnn* c, float* h_grads, size_t n);
 
+/* Inspection of the last msf_train_step (no paper counterpart: test and debug
+ * access to the intermediate tensors, so that every forward and backward
+ * kernel can be checked on its own).  msf_cnn_train_trace(c, 1) (after
+ * msf_cnn_train_reserve) makes every following step also keep the gradients
+ * between layers, 18 BF16 tensors of the reserved pixel count (off: 0 frees
+ * them).  msf_cnn_train_tensor copies one tensor of the last step to host
+ * memory (synchronises the device); bytes must be its exact size, with
+ * P = B*H*W of that step and pixels in [B][H][W] order:
+ *   MSF_TT_ACT  layer 1..9: input of conv layer l (after ReLU), BF16 [P][64]
+ *   MSF_TT_Z    layer 1..8: conv output before BatchNorm, FP32 [P][64]
+ *   MSF_TT_DZ   layer 0..8: loss gradient w.r.t. conv l's output, BF16 [P][64]
+ *               (needs the trace)
+ *   MSF_TT_DA   layer 1..9: loss gradient w.r.t. conv l's input, BF16 [P][64]
+ *               (needs the trace)
+ *   MSF_TT_R    network output R (last conv), FP32 [P]; MSF_TT_DR its gradient
+ *   MSF_TT_BN   layer 1..8: batch mean and 1/sqrt(var + eps), FP32 [2][64] */
+enum { MSF_TT_ACT = 0, MSF_TT_Z = 1, MSF_TT_DZ = 2, MSF_TT_DA = 3, MSF_TT_R = 4, MSF_TT_DR = 5, MSF_TT_BN = 6 };
+msf_status msf_cnn_train_trace(msf_cnn* c, int on);
+msf_status msf_cnn_train_tensor(msf_cnn* c, int kind, int layer, void* h_dst, size_t bytes);
+
 /* Training pairs (Sec. V: clean patches plus additive white Gaussian noise):
  * B patches of H x W with 5 channels cut from the clean volume stack d_vol
  * (vol->nt volumes of nx*ny*nz).  Each patch takes a random volume, a random

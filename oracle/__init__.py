@@ -563,6 +563,33 @@ def denoise(v4, layers, orient, emulate_bf16=False):
 # ---- training (Sec. V): MSE on (noisy, clean) pairs, BatchNorm in training mode, Adam.
 
 
+def bn_relu_forward(z, gamma, beta):
+    """BatchNorm in training mode (batch statistics over (n, i, j), biased
+    variance, eps = 1e-5) followed by ReLU on z [N,C,H,W].
+    Returns (a, y, xhat, istd, mean, var) with y = gamma xhat + beta, a = max(y, 0)."""
+    mean = z.mean(axis=(0, 2, 3))
+    var = z.var(axis=(0, 2, 3))
+    istd = 1.0 / np.sqrt(var + BN_EPS)
+    xhat = (z - mean[None, :, None, None]) * istd[None, :, None, None]
+    y = gamma[None, :, None, None] * xhat + beta[None, :, None, None]
+    return np.maximum(y, 0.0), y, xhat, istd, mean, var
+
+
+def bn_relu_backward(da, y, xhat, istd, gamma):
+    """Gradients through ReLU and training-mode BatchNorm: from the gradient da
+    of a = max(y, 0) to dz (the conv output), d gamma and d beta.  With
+    dy = da [y > 0] and m the mean over (n, i, j):
+        dz = istd (gamma dy - m(gamma dy) - xhat m(gamma dy xhat)),
+        d gamma = sum dy xhat,  d beta = sum dy."""
+    dy = da * (y > 0)
+    dgamma, dbeta = (dy * xhat).sum(axis=(0, 2, 3)), dy.sum(axis=(0, 2, 3))
+    dxh = dy * gamma[None, :, None, None]
+    m1 = dxh.mean(axis=(0, 2, 3))[None, :, None, None]
+    m2 = (dxh * xhat).mean(axis=(0, 2, 3))[None, :, None, None]
+    return istd[None, :, None, None] * (dxh - m1 - xhat * m2), dgamma, dbeta
+
+
+
 def train_forward(x, convs, bns, emulate_bf16=False):
     """Training forward; returns (out, cache).  Hidden layers: conv (+bias),
     BatchNorm with batch statistics (biased variance), ReLU.
@@ -582,16 +609,12 @@ def train_forward(x, convs, bns, emulate_bf16=False):
             a = r(np.maximum(z, 0.0))
         elif l < L - 1:
             g, be = bns[l - 1]
-            mean = z.mean(axis=(0, 2, 3))
-            var = z.var(axis=(0, 2, 3))
-            istd = 1.0 / np.sqrt(var + BN_EPS)
-            xhat = (z - mean[None, :, None, None]) * istd[None, :, None, None]
-            yv = g[None, :, None, None] * xhat + be[None, :, None, None]
+            a, yv, xhat, istd, mean, var = bn_relu_forward(z, g, be)
             cache["xhat"].append(xhat)
             cache["istd"].append(istd)
             cache["y"].append(yv)
             cache["stats"].append((mean, var))
-            a = r(np.maximum(yv, 0.0))
+            a = r(a)
         else:
             a = z
         if l < L - 1:
@@ -623,14 +646,9 @@ def train_loss_grad(x, clean, convs, bns, emulate_bf16=False):
         elif l == 0:
             dz = r(da * (c["z"][0] > 0))
         else:
-            dy = da * (c["y"][l - 1] > 0)
-            xhat, istd = c["xhat"][l - 1], c["istd"][l - 1]
-            g = bns[l - 1][0]
-            gbns[l - 1] = ((dy * xhat).sum(axis=(0, 2, 3)), dy.sum(axis=(0, 2, 3)))
-            dxh = dy * g[None, :, None, None]
-            m1 = dxh.mean(axis=(0, 2, 3))[None, :, None, None]
-            m2 = (dxh * xhat).mean(axis=(0, 2, 3))[None, :, None, None]
-            dz = r(istd[None, :, None, None] * (dxh - m1 - xhat * m2))
+            dz, dg, db = bn_relu_backward(da, c["y"][l - 1], c["xhat"][l - 1], c["istd"][l - 1], bns[l - 1][0])
+            gbns[l - 1] = (dg, db)
+            dz = r(dz)
         a_in = c["a"][l]
         gconvs[l] = (conv3x3_wgrad(dz, a_in), dz.sum(axis=(0, 2, 3)))
         if l > 0:

@@ -1310,6 +1310,12 @@ struct msf_cnn {
     int64_t train_cap = 0;
     void* train_ws = nullptr;
     size_t train_ws_bytes = 0;
+    // optional record of the inter-layer gradients of the last step
+    // (msf_cnn_train_trace): dz of layers 0..8 and da of layers 1..9, BF16 [P][64]
+    bool trace_on = false;
+    __nv_bfloat16* trace = nullptr;
+    int64_t trace_cap = 0;
+    int64_t last_P = 0;
 };
 
 static msf_status fold_all(msf_cnn* c, cudaStream_t st) {
@@ -1388,6 +1394,7 @@ extern "C" void msf_cnn_destroy(msf_cnn* c) {
     cudaFree(c->d_err);
     cudaFree(c->d_frozen);
     cudaFree(c->train_ws);
+    cudaFree(c->trace);
     delete c;
 }
 
@@ -2076,6 +2083,8 @@ __global__ void training_batch_kernel(const float* __restrict__ vol, int nx, int
 }  // namespace cnn
 }  // namespace msf
 
+static msf_status trace_alloc(msf_cnn* c);
+
 extern "C" msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels) {
     MSF_REQUIRE(c, "msf_cnn_train_reserve: NULL handle");
     MSF_REQUIRE(max_train_pixels >= 128, "msf_cnn_train_reserve: need at least 128 pixels");
@@ -2090,7 +2099,7 @@ extern "C" msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels
     }
     c->train_ws_bytes = bytes;
     c->train_cap = max_train_pixels;
-    return MSF_OK;
+    return trace_alloc(c);
 }
 
 extern "C" msf_status msf_cnn_get_grads(msf_cnn* c, float* h_grads, size_t n) {
@@ -2113,6 +2122,78 @@ extern "C" msf_status msf_training_batch(const float* d_vol, const msf_vol* vol,
     training_batch_kernel<<<152 * 8, 256, 0, st>>>(d_vol, vol->nx, vol->ny, vol->nz, vol->nt, B, H, W, (float)sigma_lo,
                                                    (float)sigma_hi, seed, d_noisy, d_clean);
     MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
+enum TraceKind { TRACE_DZ = 0, TRACE_DA = 1 };
+
+// Slot of the trace buffer: dz of layer l (0..8) in slots 0..8, da of layer l
+// (1..9) in slots 9..17; each slot holds trace_cap pixels x 64 BF16.
+static __nv_bfloat16* trace_slot(msf_cnn* c, int kind, int l) {
+    const int slot = kind == TRACE_DZ ? l : 8 + l;
+    return c->trace + (size_t)slot * c->trace_cap * CH;
+}
+
+static msf_status trace_record(msf_cnn* c, int kind, int l, const __nv_bfloat16* src, int64_t P, cudaStream_t st) {
+    if (!c->trace_on || !c->trace) return MSF_OK;
+    MSF_TRY_CUDA(cudaMemcpyAsync(trace_slot(c, kind, l), src, (size_t)P * CH * 2, cudaMemcpyDeviceToDevice, st));
+    return MSF_OK;
+}
+
+static msf_status trace_alloc(msf_cnn* c) {
+    cudaFree(c->trace);
+    c->trace = nullptr;
+    c->trace_cap = 0;
+    if (!c->trace_on || c->train_cap == 0) return MSF_OK;
+    if (cudaMalloc(&c->trace, (size_t)18 * c->train_cap * CH * 2) != cudaSuccess) {
+        cudaGetLastError();
+        c->trace_on = false;
+        return fail(MSF_ERR_NOMEM, "msf_cnn_train_trace: cannot allocate the trace");
+    }
+    c->trace_cap = c->train_cap;
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_cnn_train_trace(msf_cnn* c, int on) {
+    MSF_REQUIRE(c, "msf_cnn_train_trace: NULL handle");
+    MSF_REQUIRE(!on || c->train_cap > 0, "msf_cnn_train_trace: call msf_cnn_train_reserve first");
+    c->trace_on = on != 0;
+    return trace_alloc(c);
+}
+
+extern "C" msf_status msf_cnn_train_tensor(msf_cnn* c, int kind, int layer, void* h_dst, size_t bytes) {
+    MSF_REQUIRE(c && h_dst, "msf_cnn_train_tensor: NULL argument");
+    MSF_REQUIRE(c->last_P > 0 && c->train_ws, "msf_cnn_train_tensor: no training step has run");
+    TrainWS w;
+    train_layout(c->train_cap, &w, (uint8_t*)c->train_ws);
+    const size_t P = (size_t)c->last_P;
+    const void* src = nullptr;
+    size_t need = 0;
+    switch (kind) {
+        case MSF_TT_ACT:
+            MSF_REQUIRE(layer >= 1 && layer <= 9, "msf_cnn_train_tensor: activation layer %d not in 1..9", layer);
+            src = w.act[layer]; need = P * CH * 2; break;
+        case MSF_TT_Z:
+            MSF_REQUIRE(layer >= 1 && layer <= 8, "msf_cnn_train_tensor: pre-BatchNorm layer %d not in 1..8", layer);
+            src = w.z[layer]; need = P * CH * 4; break;
+        case MSF_TT_DZ:
+        case MSF_TT_DA:
+            MSF_REQUIRE(c->trace_on && c->trace, "msf_cnn_train_tensor: gradients need msf_cnn_train_trace(c, 1) "
+                                                 "before the step");
+            MSF_REQUIRE(kind == MSF_TT_DZ ? (layer >= 0 && layer <= 8) : (layer >= 1 && layer <= 9),
+                        "msf_cnn_train_tensor: gradient layer %d out of range", layer);
+            src = trace_slot(c, kind == MSF_TT_DZ ? TRACE_DZ : TRACE_DA, layer); need = P * CH * 2; break;
+        case MSF_TT_R: src = w.R; need = P * 4; break;
+        case MSF_TT_DR: src = w.dR; need = P * 4; break;
+        case MSF_TT_BN:
+            MSF_REQUIRE(layer >= 1 && layer <= 8, "msf_cnn_train_tensor: BatchNorm layer %d not in 1..8", layer);
+            src = w.bnp + (size_t)(layer - 1) * 2 * CH; need = 2 * CH * 4; break;
+        default:
+            return fail(MSF_ERR_ARG, "msf_cnn_train_tensor: unknown kind %d", kind);
+    }
+    MSF_REQUIRE(bytes == need, "msf_cnn_train_tensor: expected %zu bytes, got %zu", need, bytes);
+    MSF_TRY_CUDA(cudaDeviceSynchronize());
+    MSF_TRY_CUDA(cudaMemcpy(h_dst, src, need, cudaMemcpyDeviceToHost));
     return MSF_OK;
 }
 
@@ -2213,6 +2294,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     {
         MSF_PROF("train_last_bwd", st);
         last_dgrad_kernel<<<152 * 8, 256, 0, st>>>(w.dR, c->d_params, o.w[9], (uint4*)w.g[0], B, H, W);
+        MSF_TRY(trace_record(c, TRACE_DA, 9, w.g[0], P, st));
         wgrad_last_kernel<<<dim3(9, nchunks), 256, 0, st>>>(w.dR, (const uint4*)w.act[9], w.wpart, B, H, W);
         wgrad_last_reduce_kernel<<<(9 * CH + 255) / 256, 256, 0, st>>>(w.wpart, nchunks, c->d_grad + o.w[9]);
         sum_f32_kernel<<<nred, 256, 0, st>>>(w.dR, (size_t)P, w.part);
@@ -2235,6 +2317,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
                                                          (uint4*)w.g[cur ^ 1], bnp, ga, be, sums + 2 * CH, (double)P, n8);
             MSF_LAUNCH_CHECK();
         }
+        MSF_TRY(trace_record(c, TRACE_DZ, l, w.g[cur ^ 1], P, st));
         // dz in g[cur ^ 1]: conv bias grad, weight grad, input grad
         MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, sums));
         {
@@ -2248,12 +2331,14 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RAW>(g18[cur ^ 1], mb[l - 1], g4[cur], w.zeros, tg, sg, nullptr, nullptr,
                                                c->d_err, st)));
         // g[cur] now holds the gradient w.r.t. act[l]
+        MSF_TRY(trace_record(c, TRACE_DA, l, w.g[cur], P, st));
     }
     {
         MSF_PROF("train_first_bwd", st);
         relu_bwd_kernel<<<152 * 8, 256, 0, st>>>((const uint4*)w.g[cur], (const uint4*)w.act[1], (uint4*)w.g[cur ^ 1], n8);
         MSF_LAUNCH_CHECK();
     }
+    MSF_TRY(trace_record(c, TRACE_DZ, 0, w.g[cur ^ 1], P, st));
     MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, w.sums));
     {
         MSF_PROF("train_wgrad", st);
@@ -2275,6 +2360,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     }
     c->folded = false;
     c->gen += 1;
+    c->last_P = P;
     if (h_loss) {
         double l = 0.0;
         MSF_TRY_CUDA(cudaMemcpyAsync(&l, w.loss, 8, cudaMemcpyDeviceToHost, st));

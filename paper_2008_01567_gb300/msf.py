@@ -92,6 +92,8 @@ _SIGS = {
     "msf_train_step": (_I, [_P, _P, _P, _I, _I, _I, _F, ctypes.POINTER(_F), _P]),
     "msf_cnn_train_reserve": (_I, [_P, ctypes.c_int64]),
     "msf_cnn_get_grads": (_I, [_P, _P, _Z]),
+    "msf_cnn_train_trace": (_I, [_P, _I]),
+    "msf_cnn_train_tensor": (_I, [_P, _I, _I, _P, _Z]),
     "msf_training_batch": (_I, [_P, ctypes.POINTER(msf_vol), _I, _I, _I, _D, _D, ctypes.c_uint64, _P, _P, _P]),
     "msf_mace_create": (_I, [ctypes.POINTER(msf_mace_desc), ctypes.POINTER(_P)]),
     "msf_mace_destroy": (None, [_P]),
@@ -324,6 +326,28 @@ class Cnn:
 
     def train_reserve(self, pixels: int):
         _check(lib().msf_cnn_train_reserve(self.handle, int(pixels)))
+
+    def train_trace(self, on: bool):
+        _check(lib().msf_cnn_train_trace(self.handle, 1 if on else 0))
+
+    TT_ACT, TT_Z, TT_DZ, TT_DA, TT_R, TT_DR, TT_BN = range(7)
+
+    def train_tensor(self, kind: int, layer: int, P: int) -> np.ndarray:
+        """One tensor of the last training step as float64: [P][64] for
+        activations and gradients (BF16 or FP32 on the device), [P] for R and
+        dR, [2][64] (mean, 1/std) for the BatchNorm statistics."""
+        if kind in (self.TT_ACT, self.TT_DZ, self.TT_DA):
+            a = np.zeros((P, 64), dtype=np.uint16)
+        elif kind == self.TT_Z:
+            a = np.zeros((P, 64), dtype=np.float32)
+        elif kind in (self.TT_R, self.TT_DR):
+            a = np.zeros(P, dtype=np.float32)
+        else:
+            a = np.zeros((2, 64), dtype=np.float32)
+        _check(lib().msf_cnn_train_tensor(self.handle, kind, layer, a.ctypes.data, a.nbytes))
+        if a.dtype == np.uint16:
+            return (a.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return a.astype(np.float64)
 
 
 def msf_training_batch(vol_stack, vol: msf_vol, B: int, H: int, W: int, sigma_lo: float, sigma_hi: float,

@@ -166,3 +166,31 @@ def test_bf16_emulation_modes(oracle):
     _, g_b, gb_b, _ = oracle.train_loss_grad(x, clean, convs, bns, emulate_bf16=True)
     for (a, _), (b, _) in zip(g_e, g_b):
         assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(a)
+
+
+def test_bn_relu_backward_finite_differences(oracle):
+    # the standalone BatchNorm + ReLU backward against central differences of
+    # L = sum(c * a(z, gamma, beta)) for a random upstream gradient c
+    rng = np.random.default_rng(81)
+    z = rng.normal(0.3, 1.2, (3, 4, 5, 6))
+    gamma, beta = rng.uniform(0.5, 1.5, 4), rng.normal(0, 0.3, 4)
+    c = rng.normal(size=z.shape)
+
+    def L(z_, g_, b_):
+        return float(np.sum(c * oracle.bn_relu_forward(z_, g_, b_)[0]))
+
+    a, y, xhat, istd, mean, var = oracle.bn_relu_forward(z, gamma, beta)
+    dz, dg, db = oracle.bn_relu_backward(c, y, xhat, istd, gamma)
+    h = 1e-6
+    fz = np.zeros(z.size)
+    for i in range(z.size):
+        e = np.zeros(z.size); e[i] = h
+        fz[i] = (L(z + e.reshape(z.shape), gamma, beta) - L(z - e.reshape(z.shape), gamma, beta)) / (2 * h)
+    np.testing.assert_allclose(dz.ravel(), fz, rtol=1e-5, atol=1e-7)
+    for k in range(4):
+        e = np.zeros(4); e[k] = h
+        assert dg[k] == pytest.approx((L(z, gamma + e, beta) - L(z, gamma - e, beta)) / (2 * h), rel=1e-6, abs=1e-8)
+        assert db[k] == pytest.approx((L(z, gamma, beta + e) - L(z, gamma, beta - e)) / (2 * h), rel=1e-6, abs=1e-8)
+    # biased variance, mean over (n, i, j)
+    np.testing.assert_allclose(mean, z.mean(axis=(0, 2, 3)))
+    np.testing.assert_allclose(istd, 1 / np.sqrt(z.var(axis=(0, 2, 3)) + 1e-5))
