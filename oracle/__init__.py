@@ -330,6 +330,60 @@ def map_mm(y4, lam4, x4, scan, p, q, T, sx, bt, beta, n_outer, n_cg):
     return x
 
 
+# Blind correction of fixtures outside the field of view (Appendix A, Algorithm 2).
+
+
+def cylinder_mask(shape3, vox, r_mask) -> np.ndarray:
+    """1 for voxels whose centre lies within r_mask of the rotation axis (z), else 0."""
+    nz, ny, nx = shape3
+    yc = (np.arange(ny) - 0.5 * (ny - 1)) * vox
+    xc = (np.arange(nx) - 0.5 * (nx - 1)) * vox
+    inside = (xc[None, :] ** 2 + yc[:, None] ** 2) <= r_mask ** 2
+    return np.broadcast_to(inside[None], (nz, ny, nx)).astype(np.float64)
+
+
+def gaussian_taps(sigma_px: float) -> np.ndarray:
+    """Normalised Gaussian taps g_k ~ exp(-k^2 / (2 sigma^2)), |k| <= ceil(3 sigma)."""
+    R = int(math.ceil(3.0 * sigma_px))
+    k = np.arange(-R, R + 1, dtype=np.float64)
+    g = np.exp(-k * k / (2.0 * sigma_px * sigma_px))
+    return g / g.sum()
+
+
+def blur_sinogram(e4, sigma_px):
+    """Separable Gaussian blur of every view of a sinogram [..., nv, nu] along u
+    then v, detector pixels outside the detector counting as zero."""
+    g = gaussian_taps(sigma_px)
+    R = (len(g) - 1) // 2
+    out = np.array(e4, dtype=np.float64)
+    for axis in (-1, -2):
+        n = out.shape[axis]
+        pad = [(0, 0)] * out.ndim
+        pad[axis] = (R, R)
+        ep = np.pad(out, pad)
+        acc = np.zeros_like(out)
+        for j, gj in enumerate(g):
+            acc += gj * np.take(ep, np.arange(j, j + n), axis=axis)
+        out = acc
+    return out
+
+
+def fixture_correct(y4, x4, scan, r_mask, sigma_px):
+    """Algorithm 2 given the reconstruction x = recon(y, A):
+        x^m = mask(x)                  (cylinder of radius r_mask)
+        e   = y - A x^m
+        p   = blur(e)                  (separable Gaussian, sigma_px detector pixels)
+        c   = argmin_c ||e - c p||^2 = <e, p> / <p, p>   (one scalar for the scan)
+        y^corr = y - c p.
+    Returns (y_corr, c)."""
+    m = cylinder_mask(x4.shape[1:], scan.vox, r_mask)
+    e = y4 - project4d(x4 * m[None], scan)
+    p = blur_sinogram(e, sigma_px)
+    pp = float(np.sum(p * p))
+    c = float(np.sum(e * p)) / pp if pp > 0 else 0.0
+    return y4 - c * p, c
+
+
 # MACE operators.
 
 

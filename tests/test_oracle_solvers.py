@@ -390,3 +390,58 @@ def test_mace_with_exact_agents_reaches_the_map_point(oracle):
     xhat, W, X, res = oracle.mace(np.zeros((nt, n, n, n)), agents, mu, 0.5, 200)
     xmap = oracle.map_mm(y, lam, np.zeros((nt, n, n, n)), sc, p, q, T, sx, bt, mu[1] / mu[0], 300, 30)
     np.testing.assert_allclose(oracle.average(X, mu), xmap, rtol=1e-6, atol=1e-8 * np.abs(xmap).max())
+
+
+# ---------------------------------------------------------------- blind fixture correction (Appendix A)
+
+
+def test_blur_taps_and_impulse_response(oracle):
+    g = oracle.gaussian_taps(1.7)
+    assert g.sum() == pytest.approx(1.0, abs=1e-15) and len(g) == 2 * 6 + 1
+    np.testing.assert_allclose(g, g[::-1])
+    # an interior impulse spreads into the outer product of the taps
+    e = np.zeros((1, 1, 31, 37))
+    e[0, 0, 15, 18] = 1.0
+    b = oracle.blur_sinogram(e, 1.7)
+    np.testing.assert_allclose(b[0, 0, 15 - 6:15 + 7, 18 - 6:18 + 7], np.outer(g, g), rtol=1e-14, atol=1e-17)
+    assert b.sum() == pytest.approx(1.0, rel=1e-14)
+    # a constant field keeps its value away from the detector edges
+    c = oracle.blur_sinogram(np.full((2, 1, 30, 40), 2.5), 2.0)
+    np.testing.assert_allclose(c[:, :, 6:-6, 6:-6], 2.5, rtol=1e-14)
+    assert c[0, 0, 0, 0] < 2.5
+
+
+def test_fixture_correction_least_squares_and_recovery(oracle):
+    sc = synth.Scan(n=16, nt=2, nu=28, nv=24, views=5)
+    ell = synth.ellipsoids(21, 2, sc, axis_range=(0.08, 0.15))
+    ell[:, :, 0:2] *= 0.4                      # keep the object well inside the mask
+    x = oracle.ellipsoid_volume(ell, sc, ss=2)
+    y_obj = oracle.project4d(x, sc)
+    # no fixture and an exact reconstruction: nothing to correct
+    yc, c = oracle.fixture_correct(y_obj, x, sc, 0.45, 2.0)
+    assert abs(c) < 1e-12
+    np.testing.assert_allclose(yc, y_obj, atol=1e-12)
+    # a smooth fixture shadow (a broad bump drifting across the views) is removed
+    vv, uu = np.meshgrid(np.arange(sc.nv), np.arange(sc.nu), indexing="ij")
+    f = np.zeros_like(y_obj)
+    for t in range(sc.nt):
+        for j in range(sc.views):
+            f[t, j] = 0.6 * np.exp(-((uu - 4 - 3 * j) ** 2) / 40.0 - ((vv - 12) ** 2) / 200.0)
+    y = y_obj + f
+    yc, c = oracle.fixture_correct(y, x, sc, 0.45, 2.0)
+    assert np.linalg.norm(yc - y_obj) < 0.1 * np.linalg.norm(f)
+    assert 0.8 < c < 1.25
+    # c minimises ||e - c p||^2
+    m = oracle.cylinder_mask(x.shape[1:], sc.vox, 0.45)
+    e = y - oracle.project4d(x * m[None], sc)
+    p = oracle.blur_sinogram(e, 2.0)
+    r = lambda cc: float(np.sum((e - cc * p) ** 2))
+    assert r(c) <= min(r(c + 1e-3), r(c - 1e-3))
+
+
+def test_cylinder_mask(oracle):
+    m = oracle.cylinder_mask((3, 8, 8), 1.0 / 8, 0.3)
+    assert m.shape == (3, 8, 8) and set(np.unique(m)) <= {0.0, 1.0}
+    assert m[0, 3, 3] == 1.0 and m[0, 0, 0] == 0.0
+    np.testing.assert_array_equal(m, m[:, ::-1, :])
+    np.testing.assert_array_equal(m[0], m[0].T)
