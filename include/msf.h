@@ -257,6 +257,30 @@ msf_status msf_map_solve(msf_map* m, const msf_mrf* prm, double beta, const floa
 msf_status msf_map_cost(msf_map* m, const msf_mrf* prm, double beta, const float* d_y, const float* d_lambda,
                         const float* d_x, double* h_cost, void* stream);
 
+/* ------------------------------------------------------------ fixture correction (Appendix A) */
+
+/* Blind correction of fixtures outside the field of view (Appendix A,
+ * Algorithm 2): the shadow of out-of-view holders is smooth, so after removing
+ * the projection of the masked reconstruction what remains, blurred, is mostly
+ * that shadow, and a least-squares multiple of it is subtracted from y:
+ *     x^m = x inside the cylinder |(x, y)| <= r_mask about the rotation axis
+ *           (voxel centres; 0 outside),
+ *     e   = y - A x^m                       (msf_project of the plan),
+ *     p   = blur(e): every view blurred along u, then along v, by normalised
+ *           Gaussian taps g_k ~ exp(-k^2/(2 blur_sigma^2)), |k| <= ceil(3 blur_sigma)
+ *           (detector pixels; taps beyond the detector edge count as zero),
+ *     c   = <e, p> / <p, p>  (FP64, one scalar for the whole scan; 0 if p = 0),
+ *     y^corr = y - c p.
+ * d_x is the reconstruction x = recon(y, A) of the algorithm's first line (the
+ * caller's: e.g. X_0 of a MACE run); d_y, d_ycorr: sinograms (must differ);
+ * 0 < blur_sigma <= 64/3 pixels.  h_c (optional, synchronises) receives c.
+ * The workspace holds one 4D volume and two sinograms. */
+typedef struct msf_fixcorr msf_fixcorr;
+msf_status msf_fixcorr_create(msf_projector* p, msf_fixcorr** out);
+void msf_fixcorr_destroy(msf_fixcorr* f);
+msf_status msf_fixture_correct(msf_fixcorr* f, const float* d_y, const float* d_x, double r_mask, double blur_sigma,
+                               float* d_ycorr, double* h_c, void* stream);
+
 /* ------------------------------------------------------------ CNN agents */
 
 /* Agent orientation (Sec. IV): convolution plane and slicing axis.

@@ -21,6 +21,7 @@ msf_status check_device();
 // The volume a projector plan was built for, and its sinogram size (rays).
 const msf_vol* projector_volume(const msf_projector* p);
 size_t projector_sino_size(const msf_projector* p);
+void projector_detector(const msf_projector* p, int* nu, int* nv);
 
 // Device status word of a data-agent workspace: 0, or MSF_ERR_NUMERIC once a
 // CG or ICD scalar was non-finite (sticky).

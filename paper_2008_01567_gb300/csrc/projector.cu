@@ -985,6 +985,10 @@ using namespace msf;
 const msf_vol* msf::projector_volume(const msf_projector* p) { return &p->vol; }
 int* msf::dataprox_status(msf_dataprox* d) { return d->d_status; }
 size_t msf::projector_sino_size(const msf_projector* p) { return sino_size(p); }
+void msf::projector_detector(const msf_projector* p, int* nu, int* nv) {
+    *nu = p->geom.nu;
+    *nv = p->geom.nv;
+}
 
 extern "C" msf_status msf_projector_create(const msf_geom* geom, const msf_vol* vol,
                                            msf_projector** out) {

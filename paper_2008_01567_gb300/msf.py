@@ -82,6 +82,9 @@ _SIGS = {
     "msf_map_destroy": (None, [_P]),
     "msf_map_solve": (_I, [_P, ctypes.POINTER(msf_mrf), _D, _P, _P, _P, _I, _I, _P]),
     "msf_map_cost": (_I, [_P, ctypes.POINTER(msf_mrf), _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
+    "msf_fixcorr_create": (_I, [_P, ctypes.POINTER(_P)]),
+    "msf_fixcorr_destroy": (None, [_P]),
+    "msf_fixture_correct": (_I, [_P, _P, _P, _D, _D, _P, ctypes.POINTER(_D), _P]),
     "msf_prox_qggmrf": (_I, [ctypes.POINTER(msf_vol), ctypes.POINTER(msf_mrf), _P, _P, _D, _I, _P]),
     "msf_cnn_create": (_I, [ctypes.c_int64, ctypes.POINTER(_P)]),
     "msf_cnn_destroy": (None, [_P]),
@@ -287,6 +290,33 @@ def msf_map_cost(ms: MapSolver, mrf: msf_mrf, beta: float, y, lam, x, stream=Non
     c = ctypes.c_double(0.0)
     _check(lib().msf_map_cost(ms.handle, ctypes.byref(mrf), beta, _f32(y), _f32(lam), _f32(x), ctypes.byref(c),
                               _stream(stream)))
+    return c.value
+
+
+# ------------------------------------------------------------------ fixture correction
+
+
+class FixtureCorrector:
+    """Owns an msf_fixcorr workspace for a projector's problem size."""
+
+    def __init__(self, proj: Projector):
+        h = ctypes.c_void_p()
+        _check(lib().msf_fixcorr_create(proj.handle, ctypes.byref(h)))
+        self.handle = h
+        self.proj = proj
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().msf_fixcorr_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def msf_fixture_correct(fc: FixtureCorrector, y, x, r_mask: float, blur_sigma: float, ycorr, stream=None) -> float:
+    c = ctypes.c_double(0.0)
+    _check(lib().msf_fixture_correct(fc.handle, _f32(y), _f32(x), r_mask, blur_sigma, _f32(ycorr), ctypes.byref(c),
+                                     _stream(stream)))
     return c.value
 
 
