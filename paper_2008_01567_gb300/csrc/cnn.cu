@@ -1113,6 +1113,164 @@ static void launch_stencil(const float* part, long long plane, const float* bias
     resid_stencil_kernel<ORIENT><<<grid, dim3(32, 8), 0, st>>>(part, plane, bias, sg, centre, outv);
 }
 
+// ---------------------------------------------------------------- tcgen05 weight gradients (training)
+
+// Weight gradients of a 64 -> 64 3x3 layer on the tensor cores:
+//   dW[tap][co][ci] = sum_p dz[p][co] act[p + off(tap)][ci]
+// as D[(tap, ci)][co] += A[(tap, ci)][p] B[p][co] over pixel K-steps of 16.
+// Both operands are MN-major: the 128-byte rows of the TMA boxes are pixels
+// (K) holding 64 channels (M or N), exactly as the forward convolution loads
+// them.  A tile is 16 x 8 pixels; its act halo comes in three boxes (columns
+// shifted by dx = -1, 0, +1, 18 rows each) and tap (dy, dx)'s window of K-step
+// k (tile rows 2k, 2k+1) starts (2k + dy + 1) * 1024 bytes into box dx + 1.
+// Two taps share one M = 128 MMA (the second 64 rows of A start the address
+// difference of their windows further: the descriptor's leading byte offset),
+// so each K-step is five MMAs of 128 x 64 x 16; the ninth tap is paired with
+// tap 7 again and that half of the result is dropped.  Every CTA accumulates
+// its tiles (a fixed round-robin sequence) in TMEM and writes one partial
+// dW[9][64][64]; the partials are summed over CTAs in a fixed order.
+constexpr int WG_STAGES = 2;
+constexpr int WG_STAGE_BYTES = 3 * HALO_BYTES + TILE_BYTES;   // act boxes dx = -1, 0, +1, then dz
+constexpr int WG_SLACK = 40960;      // unused tail: keeps every descriptor reach inside the CTA's allocation
+constexpr int WG_SMEM = 1024 + WG_STAGES * WG_STAGE_BYTES + WG_SLACK + 256;
+constexpr int WG_TMEM_COLS = 512;    // five 64-column accumulators
+constexpr int WG_MAX_CTAS = 256;
+static_assert(WG_SMEM <= 232448, "more dynamic shared memory than a CTA may have");
+
+__host__ __device__ constexpr int wg_lo(int g) { return g == 0 ? 0 : g == 1 ? 3 : g == 2 ? 4 : g == 3 ? 6 : 7; }
+__host__ __device__ constexpr int wg_hi(int g) { return g == 0 ? 1 : g == 1 ? 2 : g == 2 ? 5 : g == 3 ? 7 : 8; }
+// byte offset of tap t's window (K-step 0) inside a stage: box dx + 1, row dy + 1
+__host__ __device__ constexpr int wg_win(int t) { return (t % 3) * HALO_BYTES + (t / 3) * 1024; }
+static_assert(wg_win(wg_hi(0)) > wg_win(wg_lo(0)) && wg_win(wg_hi(1)) > wg_win(wg_lo(1)) &&
+                  wg_win(wg_hi(2)) > wg_win(wg_lo(2)) && wg_win(wg_hi(3)) > wg_win(wg_lo(3)) &&
+                  wg_win(wg_hi(4)) > wg_win(wg_lo(4)),
+              "the second tap of an MMA pair must lie above the first (positive leading byte offset)");
+
+__global__ void __launch_bounds__(THREADS, 1)
+wgrad_tc_kernel(const __grid_constant__ CUtensorMap map_act, const __grid_constant__ CUtensorMap map_dz,
+                float* __restrict__ part, TileGeom tg, int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sS = smem;
+    uint64_t* bars = (uint64_t*)(sS + WG_STAGES * WG_STAGE_BYTES + WG_SLACK);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + WG_STAGES;
+    uint64_t* done = bars + 2 * WG_STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < WG_STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, WG_TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem_base = *tmem_slot;
+    auto give_up = [&](int code) {
+        *abort_flag = 1;
+        atomicExch(err, code);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: three act halo boxes and the dz box per tile
+            int issued[WG_STAGES] = {0, 0};
+            bool ok = true;
+            int j = 0;
+            for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++j) {
+                const int s = j % WG_STAGES, u = j / WG_STAGES;
+                if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                int img, a0, b0;
+                decode_tile(tg, tile, img, a0, b0);
+                uint8_t* dst = sS + s * WG_STAGE_BYTES;
+                tc::mbar_expect_tx(&full[s], WG_STAGE_BYTES);
+#pragma unroll
+                for (int bx = 0; bx < 3; ++bx)
+                    tc::tma_load_4d(dst + bx * HALO_BYTES, &map_act, &full[s], 0, b0 + bx - 1, a0 - 1, img);
+                tc::tma_load_4d(dst + 3 * HALO_BYTES, &map_dz, &full[s], 0, b0, a0, img);
+                issued[s] = u + 1;
+            }
+            if (!ok) {
+                give_up(MSF_ERR_TIMEOUT);
+                for (int s = 0; s < WG_STAGES; ++s)
+                    if (issued[s] > 0) tc::mbar_wait(&full[s], (issued[s] - 1) & 1, nullptr, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: 8 K-steps x 5 tap pairs per tile, all into TMEM
+            constexpr uint32_t idesc = tc::idesc_bf16_mn<128, 64>();
+            bool ok = true;
+            int j = 0;
+            for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++j) {
+                const int s = j % WG_STAGES, u = j / WG_STAGES;
+                if (!tc::mbar_wait(&full[s], u & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t st_base = tc::smem_u32(sS + s * WG_STAGE_BYTES);
+#pragma unroll
+                for (int k = 0; k < TILE_A / 2; ++k) {
+                    const uint64_t bd = tc::desc_sw128_mn(st_base + 3 * HALO_BYTES + k * 2048, 1024);
+#pragma unroll
+                    for (int g = 0; g < 5; ++g) {
+                        const uint32_t lo = st_base + wg_win(wg_lo(g)) + k * 2048;
+                        const uint64_t ad = tc::desc_sw128_mn(lo, (uint32_t)(wg_win(wg_hi(g)) - wg_win(wg_lo(g))));
+                        tc::mma_bf16(tmem_base + g * 64, ad, bd, idesc, (j | k) ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(&empty[s]);
+            }
+            if (ok) tc::mma_commit(done);
+            else give_up(MSF_ERR_TIMEOUT);
+        }
+    } else {
+        // ---------------- epilogue: TMEM lane quarter q = warp % 4 holds rows 32q..32q+31
+        const int q = warp & 3;
+        const int m = q * 32 + lane;          // accumulator row: (tap half, ci)
+        if (tc::mbar_wait(done, 0, abort_flag)) {
+            tc::fence_after_sync();
+            float* out = part + (size_t)blockIdx.x * 9 * CH * CH;
+#pragma unroll 1
+            for (int g = 0; g < 5; ++g) {
+                if (g == 4 && q < 2) continue;   // tap 7 again: dropped (warp-uniform)
+                uint32_t r[64];
+                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + g * 64;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) tc::tmem_ld16(taddr + c * 16, r + c * 16);
+                tc::tmem_ld_wait();
+                const int tap = m < 64 ? wg_lo(g) : wg_hi(g), ci = m & 63;
+                float* o = out + (size_t)tap * CH * CH + ci;
+#pragma unroll
+                for (int co = 0; co < CH; ++co) o[co * CH] = __uint_as_float(r[co]);
+            }
+        } else {
+            give_up(MSF_ERR_TIMEOUT);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem_base, WG_TMEM_COLS);
+    }
+}
+
 // ---------------------------------------------------------------- host helpers
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1245,6 +1403,7 @@ static msf_status ensure_kernel_attrs() {
                                       C1Cfg::SMEM));
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_PART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairCfg::SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
     done = true;
     return MSF_OK;
 }
@@ -1610,7 +1769,7 @@ static size_t train_layout(int64_t P, TrainWS* w, uint8_t* base) {
     t.part = (double*)take((size_t)t.nred * 2 * CH * 8);
     t.sums = (double*)take((size_t)8 * 4 * CH * 8);
     t.bnp = (float*)take((size_t)8 * 2 * CH * 4);
-    t.wpart = (float*)take((size_t)t.nchunks * 9 * CH * CH * 4);
+    t.wpart = (float*)take((size_t)(t.nchunks > WG_MAX_CTAS ? t.nchunks : WG_MAX_CTAS) * 9 * CH * CH * 4);
     size_t wp = 0;
     for (int l = 0; l < LAYERS; ++l) wp += (size_t)taps_of(l) * rows_of(l) * KPACK;
     t.wf = (__nv_bfloat16*)take(wp * 2);
@@ -2248,6 +2407,10 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     tg.tiles_b = (W + TILE_B - 1) / TILE_B;
     tg.total = B * tg.tiles_a * tg.tiles_b;
     SliceGeom sg{};
+    MSF_TRY(ensure_kernel_attrs());
+    // weight-gradient CTAs: one per SM (at most WG_MAX_CTAS), none without a tile
+    int wg_ctas = g_num_sms < WG_MAX_CTAS ? g_num_sms : WG_MAX_CTAS;
+    if (wg_ctas > tg.total) wg_ctas = tg.total;
     const int nred = w.nred;
     auto reduce = [&](int mode, const void* t0, const float* t1, const float* bnp, const float* ga,
                       const float* be, double* out) -> msf_status {
@@ -2323,9 +2486,16 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         {
             MSF_PROF("train_wgrad", st);
             copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums, c->d_grad + o.b[l], CH);
-            wgrad_kernel<9><<<dim3(9, nchunks), 256, 0, st>>>((const uint4*)w.g[cur ^ 1], (const uint4*)w.act[l],
-                                                               w.wpart, B, H, W);
-            wgrad_reduce_kernel<<<144, 256, 0, st>>>(w.wpart, nchunks, 9, 0, c->d_grad + o.w[l]);
+            MSF_LAUNCH_CHECK();
+        }
+        {
+            MSF_PROF("wgrad_tc", st);
+            wgrad_tc_kernel<<<wg_ctas, THREADS, WG_SMEM, st>>>(m18[l], g16[cur ^ 1], w.wpart, tg, c->d_err);
+            MSF_LAUNCH_CHECK();
+        }
+        {
+            MSF_PROF("wgrad_reduce", st);
+            wgrad_reduce_kernel<<<144, 256, 0, st>>>(w.wpart, wg_ctas, 9, 0, c->d_grad + o.w[l]);
             MSF_LAUNCH_CHECK();
         }
         MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RAW>(g18[cur ^ 1], mb[l - 1], g4[cur], w.zeros, tg, sg, nullptr, nullptr,

@@ -184,11 +184,32 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major operand in the same 128-byte
+// swizzled rows: each 128-byte row holds 64 consecutive M (or N) elements of one
+// K index, 8 K rows form a 1024-byte swizzle atom and consecutive 8-row groups
+// are 1024 bytes apart (stride byte offset); the next 64 elements along M start
+// `mn_stride` bytes further (leading byte offset).
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr, uint32_t mn_stride) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);        // start address
+    d |= (uint64_t)((mn_stride >> 4) & 0x3FFFu) << 16;   // leading byte offset: next 64 along M/N
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8 K rows
+    d |= (uint64_t)1 << 46;                          // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, M x N tile.
 template <int M, int N>
 __device__ __forceinline__ constexpr uint32_t idesc_bf16() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with both A and B MN-major (the transpose bits 15 and 16).
+template <int M, int N>
+__device__ __forceinline__ constexpr uint32_t idesc_bf16_mn() {
+    return idesc_bf16<M, N>() | (1u << 15) | (1u << 16);
 }
 
 }  // namespace tc
