@@ -309,9 +309,32 @@ msf_status msf_cnn_set_params(msf_cnn* c, const float* h_params, size_t n);
 msf_status msf_cnn_get_params(msf_cnn* c, float* h_params, size_t n);
 
 /* Agent H_{orient,t}: d_in, d_out are 4D volumes described by vol.
- * Each output voxel = centre - CNN(5-frame window), computed slice by slice. */
+ * Each output voxel = centre - CNN(5-frame window), computed slice by slice,
+ * time-points in chunks (as many as max_pixels holds, at most 16, unless tuned).
+ * The 64 -> 64 layers run as 32 x 8 row-pair tiles (two output rows share each
+ * input slice through an N = 128 MMA) when the slice height is even, else as
+ * 16 x 8 tiles, unless a tuning for this slice shape says otherwise. */
 msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* vol,
                        const float* d_in, float* d_out, void* stream);
+
+/* Conv launch tuning (no paper counterpart).  For the slices of `vol` in
+ * orientation `orient`, msf_denoise uses the given 64 -> 64 tile shape and
+ * `chunk` time-points per chunk (0: as many as fit, at most 16; never more
+ * than max_pixels allows).  MSF_TILE_AUTO picks row pairs for even heights;
+ * MSF_TILE_PAIR needs an even height.  The tile shape changes the order of the
+ * FP32 accumulation inside the MMAs, so outputs may differ between shapes by
+ * BF16 rounding of stored activations (both match the oracle within the
+ * agent's tolerance); the chunk size does not change results. */
+enum { MSF_TILE_AUTO = 0, MSF_TILE_16x8 = 1, MSF_TILE_PAIR = 2 };
+msf_status msf_cnn_set_tuning(msf_cnn* c, msf_orient orient, const msf_vol* vol, int tile, int chunk);
+
+/* Conv autotuner: for every orientation times msf_denoise on d_in (output to
+ * d_out, which must differ) with each tile shape that fits (row pairs, 16 x 8)
+ * and 16, 8 and 4 time-points per chunk (those below nt), and keeps the
+ * fastest for vol's slice shapes.  Synchronises.  h_choice (optional, 6 ints)
+ * receives {tile, chunk} per orientation. */
+msf_status msf_cnn_autotune(msf_cnn* c, const msf_vol* vol, const float* d_in, float* d_out, void* stream,
+                            int* h_choice);
 
 /* One training step (Sec. V): forward with BatchNorm batch statistics, MSE loss
  * mean((out - clean)^2), backward, and Adam (beta1 0.9, beta2 0.999, eps 1e-8,

@@ -1475,6 +1475,13 @@ struct msf_cnn {
     __nv_bfloat16* trace = nullptr;
     int64_t trace_cap = 0;
     int64_t last_P = 0;
+    // launch choices of msf_denoise per orientation, for one slice shape
+    // (msf_cnn_autotune / msf_cnn_set_tuning); tile 0 = by height parity
+    struct Tune {
+        int S = 0, H = 0, W = 0;   // the slice shape the choice is for (0: none)
+        int tile = 0;              // MSF_TILE_AUTO, MSF_TILE_16x8 or MSF_TILE_PAIR
+        int chunk = 0;             // time-points per chunk (0: as many as fit, at most 16)
+    } tune[3];
 };
 
 static msf_status fold_all(msf_cnn* c, cudaStream_t st) {
@@ -1598,7 +1605,10 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
                 (long long)per_frame, (long long)c->max_pixels);
     MSF_REQUIRE(per_frame * 128 < ((int64_t)1 << 40), "msf_denoise: frame too large");
     if (!c->folded) MSF_TRY(fold_all(c, st));
-    const int fchunk = (int)(c->max_pixels / per_frame < 16 ? c->max_pixels / per_frame : 16);
+    const msf_cnn::Tune& tu = c->tune[(int)orient];
+    const bool tuned = tu.S == sg.S && tu.H == sg.H && tu.W == sg.W;
+    int fchunk = (int)(c->max_pixels / per_frame < 16 ? c->max_pixels / per_frame : 16);
+    if (tuned && tu.chunk > 0 && tu.chunk < fchunk) fchunk = tu.chunk;
     const int imgs_cap = fchunk * sg.S;
     CUtensorMap m18[2], m4[2], mw[LAYERS];
     for (int b = 0; b < 2; ++b) {
@@ -1611,7 +1621,7 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
         MSF_TRY(make_w_map(&mw[l], c->d_wpack + c->wpack_off[l], taps_of(l) * rows_of(l), rows_of(l)));
     // images of even height take the row-pair kernel for the 64 -> 64 layers,
     // the last of them fused with the output layer
-    const bool pairs = sg.H % 2 == 0;
+    const bool pairs = sg.H % 2 == 0 && !(tuned && tu.tile == MSF_TILE_16x8);
     CUtensorMap p17[2], p4[2], mw10;
     if (pairs) {
         for (int b = 0; b < 2; ++b) {
@@ -1706,6 +1716,66 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
         }
     }
     return MSF_OK;
+}
+
+extern "C" msf_status msf_cnn_set_tuning(msf_cnn* c, msf_orient orient, const msf_vol* vol, int tile, int chunk) {
+    MSF_REQUIRE(c && vol, "msf_cnn_set_tuning: NULL argument");
+    MSF_REQUIRE(orient >= MSF_XY_T && orient <= MSF_ZX_T, "msf_cnn_set_tuning: bad orientation %d", (int)orient);
+    MSF_REQUIRE(tile == MSF_TILE_AUTO || tile == MSF_TILE_16x8 || tile == MSF_TILE_PAIR,
+                "msf_cnn_set_tuning: unknown tile shape %d", tile);
+    MSF_REQUIRE(chunk >= 0 && chunk <= 16, "msf_cnn_set_tuning: chunk must lie in 0..16");
+    int S, H, W;
+    if (orient == MSF_XY_T) { S = vol->nz; H = vol->ny; W = vol->nx; }
+    else if (orient == MSF_YZ_T) { S = vol->nx; H = vol->nz; W = vol->ny; }
+    else { S = vol->ny; H = vol->nx; W = vol->nz; }
+    MSF_REQUIRE(tile != MSF_TILE_PAIR || H % 2 == 0, "msf_cnn_set_tuning: row-pair tiles need an even slice height");
+    msf_cnn::Tune& t = c->tune[(int)orient];
+    t.S = S; t.H = H; t.W = W; t.tile = tile; t.chunk = chunk;
+    c->gen += 1;   // a captured MACE iteration must be captured again
+    return MSF_OK;
+}
+
+extern "C" msf_status msf_cnn_autotune(msf_cnn* c, const msf_vol* vol, const float* d_in, float* d_out, void* stream,
+                                       int* h_choice) {
+    MSF_REQUIRE(c && vol && d_in && d_out, "msf_cnn_autotune: NULL argument");
+    MSF_REQUIRE(d_in != d_out, "msf_cnn_autotune: input and output must differ");
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e0, e1;
+    MSF_TRY_CUDA(cudaEventCreate(&e0));
+    MSF_TRY_CUDA(cudaEventCreate(&e1));
+    msf_status rc = MSF_OK;
+    for (int o = 0; o < 3 && rc == MSF_OK; ++o) {
+        const msf_orient orient = (msf_orient)o;
+        const int H = o == MSF_XY_T ? vol->ny : (o == MSF_YZ_T ? vol->nz : vol->nx);
+        const int tiles[2] = {MSF_TILE_PAIR, MSF_TILE_16x8};
+        const int chunks[3] = {16, 8, 4};
+        float best = 1e30f;
+        int bt = MSF_TILE_AUTO, bc = 0;
+        for (int ti = 0; ti < 2 && rc == MSF_OK; ++ti) {
+            if (tiles[ti] == MSF_TILE_PAIR && H % 2 != 0) continue;
+            for (int ci = 0; ci < 3 && rc == MSF_OK; ++ci) {
+                if (ci > 0 && chunks[ci] >= vol->nt) continue;   // the same launches as a larger chunk
+                rc = msf_cnn_set_tuning(c, orient, vol, tiles[ti], chunks[ci]);
+                if (rc == MSF_OK) rc = msf_denoise(c, orient, vol, d_in, d_out, stream);   // warm
+                if (rc != MSF_OK) break;
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 2 && rc == MSF_OK; ++r) rc = msf_denoise(c, orient, vol, d_in, d_out, stream);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(MSF_ERR_CUDA, "msf_cnn_autotune: timing failed");
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rc == MSF_OK && ms < best) { best = ms; bt = tiles[ti]; bc = chunks[ci]; }
+            }
+        }
+        if (rc == MSF_OK) rc = msf_cnn_set_tuning(c, orient, vol, bt, bc);
+        if (h_choice && rc == MSF_OK) {
+            h_choice[2 * o] = bt;
+            h_choice[2 * o + 1] = bc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 // ====================================================================== training (Sec. V)

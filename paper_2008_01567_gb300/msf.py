@@ -92,6 +92,8 @@ _SIGS = {
     "msf_cnn_set_params": (_I, [_P, _P, _Z]),
     "msf_cnn_get_params": (_I, [_P, _P, _Z]),
     "msf_denoise": (_I, [_P, _I, ctypes.POINTER(msf_vol), _P, _P, _P]),
+    "msf_cnn_set_tuning": (_I, [_P, _I, ctypes.POINTER(msf_vol), _I, _I]),
+    "msf_cnn_autotune": (_I, [_P, ctypes.POINTER(msf_vol), _P, _P, _P, ctypes.POINTER(_I)]),
     "msf_train_step": (_I, [_P, _P, _P, _I, _I, _I, _F, ctypes.POINTER(_F), _P]),
     "msf_cnn_train_reserve": (_I, [_P, ctypes.c_int64]),
     "msf_cnn_get_grads": (_I, [_P, _P, _Z]),
@@ -389,6 +391,20 @@ def msf_training_batch(vol_stack, vol: msf_vol, B: int, H: int, W: int, sigma_lo
 
 def msf_denoise(cnn: Cnn, orient: int, vol: msf_vol, x, out, stream=None):
     _check(lib().msf_denoise(cnn.handle, orient, ctypes.byref(vol), _f32(x), _f32(out), _stream(stream)))
+
+
+MSF_TILE_AUTO, MSF_TILE_16x8, MSF_TILE_PAIR = 0, 1, 2
+
+
+def msf_cnn_set_tuning(cnn: Cnn, orient: int, vol: msf_vol, tile: int, chunk: int = 0):
+    _check(lib().msf_cnn_set_tuning(cnn.handle, orient, ctypes.byref(vol), tile, chunk))
+
+
+def msf_cnn_autotune(cnn: Cnn, vol: msf_vol, x, out, stream=None):
+    """Times the conv launch choices on x; returns {orient: (tile, chunk)}."""
+    ch = (ctypes.c_int * 6)()
+    _check(lib().msf_cnn_autotune(cnn.handle, ctypes.byref(vol), _f32(x), _f32(out), _stream(stream), ch))
+    return {o: (ch[2 * o], ch[2 * o + 1]) for o in range(3)}
 
 
 def msf_train_step(cnn: Cnn, noisy, clean, lr: float, stream=None, want_loss: bool = True):

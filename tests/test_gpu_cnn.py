@@ -180,3 +180,33 @@ def test_denoise_argument_errors(M):
     assert e.value.status == 1
     with pytest.raises(M.MsfError):
         M.msf_denoise(c, 5, vol, x, y)
+
+
+def test_conv_tuning_choices_and_autotuner(M):
+    # every tile shape and chunk size the autotuner may pick matches the oracle;
+    # the chunk size does not change a bit, the tile shape only BF16 rounding
+    import torch
+    convs, bns, stats = _net(61)
+    shape = (9, 18, 24, 20)           # even heights in every orientation (18, 18, 20)
+    v = f32(synth.uniform(62, shape, 0.0, 1.5))
+    c, layers = _gpu_net(M, convs, bns, stats, shape[1] * shape[2] * shape[3] * shape[0])
+    vol = M.msf_vol(shape[3], shape[2], shape[1], shape[0], 1.0)
+    x = _t(v)
+    for o, name in ((0, "xy"), (1, "yz"), (2, "zx")):
+        ref_R = v - oracle.denoise(v, layers, name, emulate_bf16=True)
+        outs = {}
+        for tile in (M.MSF_TILE_16x8, M.MSF_TILE_PAIR):
+            for chunk in (16, 4, 1):
+                M.msf_cnn_set_tuning(c, o, vol, tile, chunk)
+                out = torch.empty(shape, device="cuda")
+                M.msf_denoise(c, o, vol, x, out)
+                outs[(tile, chunk)] = out.cpu().numpy()
+                assert rel_l2(v - outs[(tile, chunk)], ref_R) <= 1e-2, (name, tile, chunk)
+            np.testing.assert_array_equal(outs[(tile, 16)], outs[(tile, 4)])
+            np.testing.assert_array_equal(outs[(tile, 16)], outs[(tile, 1)])
+    out = torch.empty(shape, device="cuda")
+    choice = M.msf_cnn_autotune(c, vol, x, out)
+    for o, name in ((0, "xy"), (1, "yz"), (2, "zx")):
+        assert choice[o][0] in (M.MSF_TILE_16x8, M.MSF_TILE_PAIR) and choice[o][1] in (16, 8, 4)
+        M.msf_denoise(c, o, vol, x, out)
+        assert rel_l2(v - out.cpu().numpy(), v - oracle.denoise(v, layers, name, emulate_bf16=True)) <= 1e-2
