@@ -317,6 +317,19 @@ msf_status msf_cnn_get_params(msf_cnn* c, float* h_params, size_t n);
 msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* vol,
                        const float* d_in, float* d_out, void* stream);
 
+/* The agent H_{orient,t} of several problems at once (Sec. IV; the batch of
+ * uneven problems): d_in[i], d_out[i] are problem i's 4D volumes vols[i], each
+ * with its own handle cnns[i] (its activation workspace; handles must differ).
+ * Every handle must hold the same parameters.  Problems whose time-points all
+ * fit in one chunk of their handle and whose slices take row-pair tiles run
+ * their 64 -> 64 layers together: one persistent launch per layer walks a work
+ * list of (problem, tile) over all of them, with the first handle's weights;
+ * their first layers and output stencils run per problem.  Other problems run
+ * msf_denoise on their own.  Results equal msf_denoise's bit for bit.  At most
+ * 16 problems. */
+msf_status msf_denoise_batch(msf_cnn* const* cnns, int n, msf_orient orient, const msf_vol* vols,
+                             const float* const* d_in, float* const* d_out, void* stream);
+
 /* Conv launch tuning (no paper counterpart).  For the slices of `vol` in
  * orientation `orient`, msf_denoise uses the given 64 -> 64 tile shape and
  * `chunk` time-points per chunk (0: as many as fit, at most 16; never more
@@ -464,8 +477,13 @@ msf_status msf_mace_consensus(float* d_W, const float* d_X, int K1, size_t N, co
 /* A queue of independent (uneven) MACE problems advanced together: each
  * problem runs on its own internal stream forked from the caller's stream and
  * joined back, so small problems share the GPU; with use_graph set for every
- * problem the whole batch iteration is one captured CUDA graph.  Problems must
- * not share a projector plan or a CNN handle (their workspaces). */
+ * problem the whole batch iteration is one captured CUDA graph.  When every
+ * problem runs the three CNN agents and all their handles hold the same
+ * parameters (checked on the host whenever a handle's parameters change), the
+ * data agents run forked as above and each orientation's CNN agents of all
+ * problems run through msf_denoise_batch (multi-problem persistent launches).
+ * Either way the results equal per-problem msf_mace_step bit for bit.
+ * Problems must not share a projector plan or a CNN handle (their workspaces). */
 typedef struct msf_mace_batch msf_mace_batch;
 msf_status msf_mace_batch_create(msf_mace** problems, int n, msf_mace_batch** out);
 void msf_mace_batch_destroy(msf_mace_batch* b);

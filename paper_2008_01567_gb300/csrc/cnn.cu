@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <string.h>
+
 #include <vector>
 
 #include "common.cuh"
@@ -775,12 +777,9 @@ __device__ __forceinline__ void decode_pair_tile(const TileGeom& tg, int tile, i
 // row (map_w10: [9 taps][64], rows 9-15 zero-filled).  Column t of that product
 // is P_t(p) = sum_c w10[t][c] act(p, c), written to part[t * plane + p];
 // resid_stencil_kernel then forms R(p) = bias + sum_t P_t(p + offset_t).
-template <int EPI>
-__global__ void __launch_bounds__(THREADS, 1)
-conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
-                 const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_w10,
-                 const float* __restrict__ bias, TileGeom tg, int* __restrict__ err, float* __restrict__ part,
-                 long long plane) {
+template <int EPI, class Src>
+__device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap* map_w, const CUtensorMap* map_w10,
+                                               const float* __restrict__ bias, int* __restrict__ err) {
     static_assert(EPI == EPI_RELU || EPI == EPI_PART, "row-pair conv: ReLU layers only");
     constexpr bool FUSED = EPI == EPI_PART;
     using C = PairCfg;
@@ -847,13 +846,15 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             tc::mbar_expect_tx(wbar, C::W_BYTES + (FUSED ? C::W10_BYTES : 0));
             for (int dx = 0; dx < 3; ++dx)
                 for (int d = 0; d < 3; ++d)
-                    tc::tma_load_2d(sW + (dx * 3 + d) * WBLK, &map_w, wbar, 0, ((2 - d) * 3 + dx) * CH);
-            if (FUSED) tc::tma_load_2d(sW10, &map_w10, wbar, 0, 0);
+                    tc::tma_load_2d(sW + (dx * 3 + d) * WBLK, map_w, wbar, 0, ((2 - d) * 3 + dx) * CH);
+            if (FUSED) tc::tma_load_2d(sW10, map_w10, wbar, 0, 0);
             int j = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x) {
+            typename Src::Cursor cur;
+            for (int tile = blockIdx.x; ok && tile < src.total(); tile += gridDim.x) {
                 int img, a0, b0;
-                decode_pair_tile(tg, tile, img, a0, b0);
+                const int job = src.locate(tile, cur);
+                decode_pair_tile(src.geom(job), cur.local, img, a0, b0);
 #pragma unroll
                 for (int p = 0; p < 2; ++p, ++j) {
                     const int s = j % NS, u = j / NS;
@@ -866,7 +867,7 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                     // parity p: box entry k is image row a0 - p + 2k (zero-filled outside the image)
 #pragma unroll
                     for (int bx = 0; bx < 3; ++bx)
-                        tc::tma_load_5d(dst + bx * PBOX_BYTES, &map_a, &full[s], 0, b0 + bx - 1, p, a0 / 2 - p, img);
+                        tc::tma_load_5d(dst + bx * PBOX_BYTES, src.map_a(job), &full[s], 0, b0 + bx - 1, p, a0 / 2 - p, img);
                     issued[s] = u + 1;
                 }
             }
@@ -899,7 +900,7 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 return true;
             };
             int it = 0, j = 0;
-            for (int tile = blockIdx.x; ok && tile < tg.total; tile += gridDim.x, ++it) {
+            for (int tile = blockIdx.x; ok && tile < src.total(); tile += gridDim.x, ++it) {
                 const int ab = it & 1, ua = it >> 1;
                 if (ua > 0 && !tc::mbar_wait(&tempty[ab], (ua - 1) & 1, abort_flag)) { ok = false; break; }
                 tc::fence_after_sync();
@@ -953,7 +954,8 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
         // holds row pairs 4q .. 4q + 3 of the tile
         const int q = warp & 3;
         int it = 0;
-        for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
+        typename Src::Cursor cur;
+        for (int tile = blockIdx.x; tile < src.total(); tile += gridDim.x, ++it) {
             const int ab = it & 1, ua = it >> 1;
             if (!tc::mbar_wait(&tfull[ab], ua & 1, abort_flag)) {
                 give_up(MSF_ERR_TIMEOUT);
@@ -961,7 +963,9 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             }
             tc::fence_after_sync();
             int img, a0, b0;
-            decode_pair_tile(tg, tile, img, a0, b0);
+            const int job = src.locate(tile, cur);
+            const TileGeom& tg = src.geom(job);
+            decode_pair_tile(tg, cur.local, img, a0, b0);
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 uint32_t r[CH];
@@ -1004,7 +1008,7 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                     if (lane == 0) {
                         // group g of this warp: 4 pair rows x 8 pixels, one bulk store
                         const int pr = a0 / 2 + 4 * q;
-                        if (pr < tg.H / 2) tc::tma_store_5d(&map_out, stage, 0, b0, g, pr, img);
+                        if (pr < tg.H / 2) tc::tma_store_5d(src.map_out(job), stage, 0, b0, g, pr, img);
                         tc::tma_store_commit();
                     }
                 }
@@ -1028,7 +1032,8 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
                 for (int g = 0; g < 2; ++g) {
                     const int a = a0 + 2 * (4 * q + (lane >> 3)) + g, b = b0 + (lane & 7);
                     if (a < tg.H && b < tg.W) {
-                        float* dst = part + ((size_t)img * tg.H + a) * tg.W + b;
+                        float* dst = src.part(job) + ((size_t)img * tg.H + a) * tg.W + b;
+                        const long long plane = src.plane(job);
 #pragma unroll
                         for (int t = 0; t < 9; ++t) dst[(size_t)t * plane] = __uint_as_float(pv[g][t]);
                     }
@@ -1043,6 +1048,81 @@ conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem_base, TMEM_PAIR);
     }
+}
+
+// Tile sources of the row-pair layer.  One problem: the launch's own maps and
+// geometry.  Several problems (one persistent launch over a batch): a work list
+// of jobs, each with its activation maps (kernel parameters, so TMA reads them
+// from the parameter space), its tile geometry and the first global tile index;
+// a CTA walks the global tiles blockIdx.x, blockIdx.x + gridDim.x, ... and finds
+// each tile's job by advancing a cursor (its tiles increase monotonically).
+struct PairSingle {
+    const CUtensorMap* a;
+    const CUtensorMap* out;
+    TileGeom tg;
+    float* part_;
+    long long plane_;
+    struct Cursor { int local = 0; };
+    __device__ __forceinline__ int total() const { return tg.total; }
+    __device__ __forceinline__ int locate(int tile, Cursor& c) const { c.local = tile; return 0; }
+    __device__ __forceinline__ const TileGeom& geom(int) const { return tg; }
+    __device__ __forceinline__ const CUtensorMap* map_a(int) const { return a; }
+    __device__ __forceinline__ const CUtensorMap* map_out(int) const { return out; }
+    __device__ __forceinline__ float* part(int) const { return part_; }
+    __device__ __forceinline__ long long plane(int) const { return plane_; }
+};
+
+constexpr int PAIR_MAX_JOBS = 16;
+
+struct PairJob {
+    CUtensorMap a;       // activations in, (pairs x parity) view with the 17-pair box
+    CUtensorMap out;     // activations out, 4-pair box (EPI_RELU)
+    TileGeom tg;         // row-pair tiles of this problem's images
+    int tile0;           // first global tile of this job
+    float* part;         // EPI_PART: per-tap planes of this problem
+    long long plane;
+};
+
+struct PairJobs {
+    PairJob job[PAIR_MAX_JOBS];
+    int n, total;
+};
+
+struct PairMulti {
+    const PairJobs* J;
+    struct Cursor { int job = 0, local = 0; };
+    __device__ __forceinline__ int total() const { return J->total; }
+    __device__ __forceinline__ int locate(int tile, Cursor& c) const {
+        while (c.job + 1 < J->n && tile >= J->job[c.job + 1].tile0) ++c.job;
+        c.local = tile - J->job[c.job].tile0;
+        return c.job;
+    }
+    __device__ __forceinline__ const TileGeom& geom(int j) const { return J->job[j].tg; }
+    __device__ __forceinline__ const CUtensorMap* map_a(int j) const { return &J->job[j].a; }
+    __device__ __forceinline__ const CUtensorMap* map_out(int j) const { return &J->job[j].out; }
+    __device__ __forceinline__ float* part(int j) const { return J->job[j].part; }
+    __device__ __forceinline__ long long plane(int j) const { return J->job[j].plane; }
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(THREADS, 1)
+conv_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
+                 const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_w10,
+                 const float* __restrict__ bias, TileGeom tg, int* __restrict__ err, float* __restrict__ part,
+                 long long plane) {
+    PairSingle src{&map_a, &map_out, tg, part, plane};
+    conv_pair_body<EPI>(src, &map_w, &map_w10, bias, err);
+}
+
+// The same layer over a batch of problems in one persistent launch (shared
+// weights and bias).
+template <int EPI>
+__global__ void __launch_bounds__(THREADS, 1)
+conv_pair_multi_kernel(const __grid_constant__ PairJobs jobs, const __grid_constant__ CUtensorMap map_w,
+                       const __grid_constant__ CUtensorMap map_w10, const float* __restrict__ bias,
+                       int* __restrict__ err) {
+    PairMulti src{&jobs};
+    conv_pair_body<EPI>(src, &map_w, &map_w10, bias, err);
 }
 
 // Output layer from the per-tap planes of EPI_PART:
@@ -1404,6 +1484,10 @@ static msf_status ensure_kernel_attrs() {
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_PART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairCfg::SMEM));
     MSF_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_multi_kernel<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      PairCfg::SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_multi_kernel<EPI_PART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      PairCfg::SMEM));
     done = true;
     return MSF_OK;
 }
@@ -1585,6 +1669,59 @@ extern "C" msf_status msf_cnn_get_params(msf_cnn* c, float* h_params, size_t n) 
     return MSF_OK;
 }
 
+// Layer 1 of one chunk (time-points sg.t0 .. sg.t0 + sg.nframes - 1): the
+// frames the chunk reads are brought into the agent's [S][H][W] order, then the
+// fused first layer writes the 64-channel activations into c->d_act[1].
+static msf_status first_layer(msf_cnn* c, const SliceGeom& sg, const msf_vol* vol, msf_orient orient,
+                              const float* d_in, const CUtensorMap& mw0, const CUtensorMap& m1o, int64_t per_frame,
+                              cudaStream_t st) {
+    const int t0 = sg.t0;
+    // the time-points this chunk reads, in the agent's [S][H][W] order
+    PackFrames pf;
+    pf.first = t0 - 2 > 0 ? t0 - 2 : 0;
+    const int last = t0 + sg.nframes + 1 < vol->nt - 1 ? t0 + sg.nframes + 1 : vol->nt - 1;
+    pf.count = last - pf.first + 1;
+    MSF_REQUIRE(pf.count <= 20 && (int64_t)pf.count * per_frame <= 5 * c->max_pixels,
+                "msf_denoise: internal frame window too large");
+    for (int k = 0; k < pf.count; ++k) {
+        const float* src = d_in + (size_t)(pf.first + k) * per_frame;
+        if (orient == MSF_XY_T) {
+            pf.f[k] = src;
+        } else {
+            float* dst = c->d_frames + (size_t)k * per_frame;
+            const long long rows = orient == MSF_YZ_T ? (long long)vol->nz * vol->ny : vol->nz;
+            const long long cols = orient == MSF_YZ_T ? vol->nx : (long long)vol->ny * vol->nx;
+            MSF_PROF("orient_transpose", st);
+            orient_transpose_kernel<<<dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)),
+                                      dim3(32, 8), 0, st>>>(src, dst, rows, cols);
+            MSF_LAUNCH_CHECK();
+            pf.f[k] = dst;
+        }
+    }
+    // first layer straight from the frames
+    TileGeom t1;
+    t1.H = sg.H; t1.W = sg.W; t1.imgs = sg.nframes * sg.S;
+    t1.tiles_a = (sg.H + C1_ROWS - 1) / C1_ROWS;
+    t1.tiles_b = (sg.W + C1_COLS - 1) / C1_COLS;
+    t1.total = t1.imgs * t1.tiles_a * t1.tiles_b;
+    MSF_TRY(ensure_kernel_attrs());
+    MSF_PROF("conv1_tc", st);
+    // the patch ring needs the frames consecutive (they are: the input
+    // volume or the transposed copies) and rows of a multiple of 16 bytes
+    const int grid1 = t1.total < g_num_sms ? t1.total : g_num_sms;
+    if (sg.W % 4 == 0) {
+        CUtensorMap mf;
+        MSF_TRY(make_frame_map(&mf, pf.f[0], sg.S, sg.H, sg.W, pf.count));
+        conv1_fused_kernel<true><<<grid1, C1_THREADS, C1Cfg::SMEM, st>>>(mw0, m1o, mf, c->d_bias, pf, sg, t1,
+                                                                           c->d_err);
+    } else {
+        conv1_fused_kernel<false><<<grid1, C1_THREADS, C1Cfg::SMEM, st>>>(mw0, m1o, m1o, c->d_bias, pf, sg,
+                                                                            t1, c->d_err);
+    }
+    MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
 extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* vol, const float* d_in,
                                   float* d_out, void* stream) {
     MSF_REQUIRE(c && vol && d_in && d_out, "msf_denoise: NULL argument");
@@ -1633,51 +1770,7 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
     for (int t0 = 0; t0 < vol->nt; t0 += fchunk) {
         sg.t0 = t0;
         sg.nframes = fchunk < vol->nt - t0 ? fchunk : vol->nt - t0;
-        {
-            // the time-points this chunk reads, in the agent's [S][H][W] order
-            PackFrames pf;
-            pf.first = t0 - 2 > 0 ? t0 - 2 : 0;
-            const int last = t0 + sg.nframes + 1 < vol->nt - 1 ? t0 + sg.nframes + 1 : vol->nt - 1;
-            pf.count = last - pf.first + 1;
-            MSF_REQUIRE(pf.count <= 20 && (int64_t)pf.count * per_frame <= 5 * c->max_pixels,
-                        "msf_denoise: internal frame window too large");
-            for (int k = 0; k < pf.count; ++k) {
-                const float* src = d_in + (size_t)(pf.first + k) * per_frame;
-                if (orient == MSF_XY_T) {
-                    pf.f[k] = src;
-                } else {
-                    float* dst = c->d_frames + (size_t)k * per_frame;
-                    const long long rows = orient == MSF_YZ_T ? (long long)vol->nz * vol->ny : vol->nz;
-                    const long long cols = orient == MSF_YZ_T ? vol->nx : (long long)vol->ny * vol->nx;
-                    MSF_PROF("orient_transpose", st);
-                    orient_transpose_kernel<<<dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)),
-                                              dim3(32, 8), 0, st>>>(src, dst, rows, cols);
-                    MSF_LAUNCH_CHECK();
-                    pf.f[k] = dst;
-                }
-            }
-            // first layer straight from the frames
-            TileGeom t1;
-            t1.H = sg.H; t1.W = sg.W; t1.imgs = sg.nframes * sg.S;
-            t1.tiles_a = (sg.H + C1_ROWS - 1) / C1_ROWS;
-            t1.tiles_b = (sg.W + C1_COLS - 1) / C1_COLS;
-            t1.total = t1.imgs * t1.tiles_a * t1.tiles_b;
-            MSF_TRY(ensure_kernel_attrs());
-            MSF_PROF("conv1_tc", st);
-            // the patch ring needs the frames consecutive (they are: the input
-            // volume or the transposed copies) and rows of a multiple of 16 bytes
-            const int grid1 = t1.total < g_num_sms ? t1.total : g_num_sms;
-            if (sg.W % 4 == 0) {
-                CUtensorMap mf;
-                MSF_TRY(make_frame_map(&mf, pf.f[0], sg.S, sg.H, sg.W, pf.count));
-                conv1_fused_kernel<true><<<grid1, C1_THREADS, C1Cfg::SMEM, st>>>(mw[0], m1o, mf, c->d_bias, pf, sg, t1,
-                                                                                   c->d_err);
-            } else {
-                conv1_fused_kernel<false><<<grid1, C1_THREADS, C1Cfg::SMEM, st>>>(mw[0], m1o, m1o, c->d_bias, pf, sg,
-                                                                                    t1, c->d_err);
-            }
-            MSF_LAUNCH_CHECK();
-        }
+        MSF_TRY(first_layer(c, sg, vol, orient, d_in, mw[0], m1o, per_frame, st));
         TileGeom tg;
         tg.H = sg.H; tg.W = sg.W; tg.imgs = sg.nframes * sg.S;
         tg.tiles_a = (sg.H + TILE_A - 1) / TILE_A;
@@ -1714,6 +1807,129 @@ extern "C" msf_status msf_denoise(msf_cnn* c, msf_orient orient, const msf_vol* 
                                                             c->d_bias + (LAYERS - 1) * CH, tg, sg, d_in, d_out,
                                                             c->d_err, st)));
         }
+    }
+    return MSF_OK;
+}
+
+// The slices of `vol` in orientation `orient`.
+static SliceGeom slice_geom(msf_orient orient, const msf_vol* vol) {
+    SliceGeom sg;
+    sg.orient = (int)orient;
+    sg.nx = vol->nx; sg.ny = vol->ny; sg.nz = vol->nz; sg.nt = vol->nt;
+    if (orient == MSF_XY_T) { sg.S = vol->nz; sg.H = vol->ny; sg.W = vol->nx; }
+    else if (orient == MSF_YZ_T) { sg.S = vol->nx; sg.H = vol->nz; sg.W = vol->ny; }
+    else { sg.S = vol->ny; sg.H = vol->nx; sg.W = vol->nz; }
+    set_strides(sg);
+    sg.t0 = 0;
+    sg.nframes = vol->nt;
+    return sg;
+}
+
+extern "C" msf_status msf_denoise_batch(msf_cnn* const* cnns, int n, msf_orient orient, const msf_vol* vols,
+                                        const float* const* d_in, float* const* d_out, void* stream) {
+    MSF_REQUIRE(cnns && vols && d_in && d_out && n > 0, "msf_denoise_batch: NULL argument or empty batch");
+    MSF_REQUIRE(n <= PAIR_MAX_JOBS, "msf_denoise_batch: at most %d problems", PAIR_MAX_JOBS);
+    MSF_REQUIRE(orient >= MSF_XY_T && orient <= MSF_ZX_T, "msf_denoise_batch: bad orientation %d", (int)orient);
+    for (int p = 0; p < n; ++p) {
+        MSF_REQUIRE(cnns[p] && d_in[p] && d_out[p] && d_in[p] != d_out[p], "msf_denoise_batch: problem %d: bad pointers", p);
+        for (int q = 0; q < p; ++q)
+            MSF_REQUIRE(cnns[q] != cnns[p], "msf_denoise_batch: problems %d and %d share a handle (its workspace)", q, p);
+    }
+    cudaStream_t st = as_stream(stream);
+    MSF_TRY(ensure_kernel_attrs());
+    struct Prob {
+        msf_cnn* c;
+        int idx;
+        SliceGeom sg;
+        int64_t per_frame;
+        CUtensorMap p17[2], p4[2], mw0, m1o;
+        TileGeom tp;
+        long long plane;
+    };
+    std::vector<Prob> batch;
+    for (int p = 0; p < n; ++p) {
+        msf_cnn* c = cnns[p];
+        const msf_vol* vol = &vols[p];
+        MSF_REQUIRE(vol->nx > 0 && vol->ny > 0 && vol->nz > 0 && vol->nt > 0, "msf_denoise_batch: bad volume %d", p);
+        const SliceGeom sg = slice_geom(orient, vol);
+        const int64_t per_frame = (int64_t)sg.S * sg.H * sg.W;
+        const msf_cnn::Tune& tu = c->tune[(int)orient];
+        const bool tuned = tu.S == sg.S && tu.H == sg.H && tu.W == sg.W;
+        int64_t fchunk = c->max_pixels / per_frame < 16 ? c->max_pixels / per_frame : 16;
+        if (tuned && tu.chunk > 0 && tu.chunk < fchunk) fchunk = tu.chunk;
+        const bool pairs = sg.H % 2 == 0 && !(tuned && tu.tile == MSF_TILE_16x8);
+        if (!pairs || fchunk < vol->nt || per_frame * 128 >= ((int64_t)1 << 40)) {
+            // not in one row-pair chunk: this problem runs on its own
+            MSF_TRY(msf_denoise(c, orient, vol, d_in[p], d_out[p], stream));
+            continue;
+        }
+        if (!c->folded) MSF_TRY(fold_all(c, st));
+        Prob b;
+        b.c = c;
+        b.idx = p;
+        b.sg = sg;
+        b.per_frame = per_frame;
+        const int imgs = vol->nt * sg.S;
+        for (int k = 0; k < 2; ++k) {
+            MSF_TRY(make_pair_map(&b.p17[k], c->d_act[k], imgs, sg.H, sg.W, PAIR_ROWS + 1));
+            MSF_TRY(make_pair_map(&b.p4[k], c->d_act[k], imgs, sg.H, sg.W, 4));
+        }
+        MSF_TRY(make_w_map(&b.mw0, c->d_wpack + c->wpack_off[0], taps_of(0) * rows_of(0), rows_of(0)));
+        MSF_TRY(make_act_map(&b.m1o, c->d_act[1], imgs, sg.H, sg.W, 1, C1_COLS));
+        b.tp.H = sg.H; b.tp.W = sg.W; b.tp.imgs = imgs;
+        b.tp.tiles_a = (sg.H + 2 * PAIR_ROWS - 1) / (2 * PAIR_ROWS);
+        b.tp.tiles_b = (sg.W + TILE_B - 1) / TILE_B;
+        b.tp.total = imgs * b.tp.tiles_a * b.tp.tiles_b;
+        b.plane = (long long)imgs * sg.H * sg.W;
+        batch.push_back(b);
+    }
+    if (batch.empty()) return MSF_OK;
+    // the 64 -> 64 layers' weights and biases: the first batched handle's
+    // (every handle of a batch holds the same parameters)
+    msf_cnn* c0 = batch[0].c;
+    CUtensorMap mw[LAYERS], mw10;
+    for (int l = 1; l < LAYERS - 1; ++l)
+        MSF_TRY(make_w_map(&mw[l], c0->d_wpack + c0->wpack_off[l], taps_of(l) * rows_of(l), rows_of(l)));
+    MSF_TRY(make_w10_map(&mw10, c0->d_wpack + c0->wpack_off[LAYERS - 1]));
+    for (Prob& b : batch)
+        MSF_TRY(first_layer(b.c, b.sg, &vols[b.idx], orient, d_in[b.idx], b.mw0, b.m1o, b.per_frame, st));
+    PairJobs J;
+    memset(&J, 0, sizeof(J));
+    J.n = (int)batch.size();
+    J.total = 0;
+    for (int i = 0; i < J.n; ++i) {
+        J.job[i].tg = batch[i].tp;
+        J.job[i].tile0 = J.total;
+        J.job[i].plane = batch[i].plane;
+        J.total += batch[i].tp.total;
+    }
+    const int grid = J.total < g_num_sms ? J.total : g_num_sms;
+    int cur = 1;
+    for (int l = 1; l < LAYERS - 1; ++l) {
+        const bool last = l == LAYERS - 2;
+        for (int i = 0; i < J.n; ++i) {
+            J.job[i].a = batch[i].p17[cur];
+            J.job[i].out = batch[i].p4[cur ^ 1];
+            J.job[i].part = last ? reinterpret_cast<float*>(batch[i].c->d_act[cur ^ 1]) : nullptr;
+        }
+        MSF_PROF(last ? "conv3x3_out_tc" : "conv3x3_tc", st);
+        if (last)
+            conv_pair_multi_kernel<EPI_PART><<<grid, THREADS, PairCfg::SMEM, st>>>(J, mw[l], mw10, c0->d_bias + l * CH,
+                                                                                  c0->d_err);
+        else
+            conv_pair_multi_kernel<EPI_RELU><<<grid, THREADS, PairCfg::SMEM, st>>>(J, mw[l], mw10, c0->d_bias + l * CH,
+                                                                                  c0->d_err);
+        MSF_LAUNCH_CHECK();
+        cur ^= 1;
+    }
+    for (Prob& b : batch) {
+        MSF_PROF("resid_stencil", st);
+        const float* part = reinterpret_cast<const float*>(b.c->d_act[cur]);
+        const float* b10 = b.c->d_bias + (LAYERS - 1) * CH;
+        if (orient == MSF_XY_T) launch_stencil<0>(part, b.plane, b10, b.sg, d_in[b.idx], d_out[b.idx], st);
+        else if (orient == MSF_YZ_T) launch_stencil<1>(part, b.plane, b10, b.sg, d_in[b.idx], d_out[b.idx], st);
+        else launch_stencil<2>(part, b.plane, b10, b.sg, d_in[b.idx], d_out[b.idx], st);
+        MSF_LAUNCH_CHECK();
     }
     return MSF_OK;
 }

@@ -45,6 +45,10 @@ struct msf_mace_batch {
     cudaGraphExec_t gexec = nullptr;
     std::vector<msf_mace_params> gprm;
     std::vector<uint64_t> gcnn;
+    // every problem runs the three CNN agents with the same parameters: the
+    // agents of all problems then run as multi-problem persistent launches
+    bool shared = false;
+    std::vector<uint64_t> shared_gen;   // CNN generations the flag was decided for
 };
 
 namespace msf {
@@ -195,6 +199,25 @@ static msf_status check_params(const msf_mace* m, const msf_mace_params* prm) {
     return MSF_OK;
 }
 
+static msf_status enqueue_data(msf_mace* m, const msf_mace_params* prm, void* sp) {
+    const msf_mace_desc& d = m->desc;
+    if (prm->n_icd > 0) return msf_prox_data_icd(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_icd, sp);
+    return msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, sp);
+}
+
+static msf_status enqueue_consensus(msf_mace* m, const msf_mace_params* prm, cudaStream_t st) {
+    const msf_mace_desc& d = m->desc;
+    const int K1 = d.K + 1;
+    MaceCoef c;
+    for (int i = 0; i < 4; ++i) c.mu[i] = i < K1 ? (float)prm->mu[i] : 0.0f;
+    c.two_rho = (float)(2.0 * prm->rho);
+    c.K1 = K1;
+    MSF_TRY(launch_consensus(d.d_W, d.d_X, K1, m->N, c, m->d_partial, m->d_sums, st));
+    MSF_TRY_CUDA(cudaMemcpyAsync(m->h_sums, m->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MSF_TRY_CUDA(cudaMemcpyAsync(m->h_status, dataprox_status(m->dp), sizeof(int), cudaMemcpyDeviceToHost, st));
+    return MSF_OK;
+}
+
 // Enqueues one whole iteration on st, ending with the copy of the two FP64
 // residual sums into the handle's pinned buffer.
 static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStream_t st) {
@@ -217,10 +240,7 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
     void* sp = reinterpret_cast<void*>(fork ? m->s_prox : st);
     void* sa = reinterpret_cast<void*>(fork ? m->s_prior : st);
     // X_0 <- L~(W_0; X_0): n_cg CG iterations, or n_icd grouped-ICD sweeps
-    if (prm->n_icd > 0)
-        MSF_TRY(msf_prox_data_icd(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_icd, sp));
-    else
-        MSF_TRY(msf_prox_data(m->dp, d.d_y, d.d_lambda, d.d_W, d.d_X, prm->sigma, prm->n_cg, sp));
+    MSF_TRY(enqueue_data(m, prm, sp));
     // X_k <- H_k(W_k)
     for (int k = 1; k < K1; ++k) {
         if (d.prior == MSF_PRIOR_QGGMRF) {
@@ -237,14 +257,8 @@ static msf_status enqueue_step(msf_mace* m, const msf_mace_params* prm, cudaStre
         MSF_TRY_CUDA(cudaStreamWaitEvent(st, m->ev_prior, 0));
     }
     // Z <- G(2X - W);  W <- W + 2 rho (Z - X)
-    MaceCoef c;
-    for (int i = 0; i < 4; ++i) c.mu[i] = i < K1 ? (float)prm->mu[i] : 0.0f;
-    c.two_rho = (float)(2.0 * prm->rho);
-    c.K1 = K1;
-    MSF_TRY(launch_consensus(d.d_W, d.d_X, K1, N, c, m->d_partial, m->d_sums, st));
-    MSF_TRY_CUDA(cudaMemcpyAsync(m->h_sums, m->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MSF_TRY_CUDA(cudaMemcpyAsync(m->h_status, dataprox_status(m->dp), sizeof(int), cudaMemcpyDeviceToHost, st));
-    return MSF_OK;
+    (void)N;
+    return enqueue_consensus(m, prm, st);
 }
 
 static msf_status read_residual(const msf_mace* m, double* h_residual) {
@@ -284,8 +298,70 @@ static msf_status capture(cudaStream_t cap, cudaGraphExec_t* out, F&& body) {
     return MSF_OK;
 }
 
+// Shared-CNN batch: the data agents on the problem streams (forked, joined),
+// then each orientation's CNN agents of all problems as multi-problem
+// persistent launches (msf_denoise_batch), then the consensus of every problem.
+static msf_status enqueue_batch_shared(msf_mace_batch* b, const msf_mace_params* prm, cudaStream_t st) {
+    const int n = (int)b->items.size();
+    MSF_TRY_CUDA(cudaEventRecord(b->fork, st));
+    for (int i = 0; i < n; ++i) {
+        MSF_TRY_CUDA(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+        MSF_TRY(enqueue_data(b->items[i], &prm[i], reinterpret_cast<void*>(b->streams[i])));
+        MSF_TRY_CUDA(cudaEventRecord(b->done[i], b->streams[i]));
+        MSF_TRY_CUDA(cudaStreamWaitEvent(st, b->done[i], 0));
+    }
+    std::vector<msf_cnn*> cnns(n);
+    std::vector<msf_vol> vols(n);
+    std::vector<const float*> in(n);
+    std::vector<float*> out(n);
+    for (int k = 1; k <= 3; ++k) {
+        for (int i = 0; i < n; ++i) {
+            msf_mace* m = b->items[i];
+            cnns[i] = m->desc.cnn;
+            vols[i] = *projector_volume(m->desc.proj);
+            in[i] = m->desc.d_W + k * m->N;
+            out[i] = m->desc.d_X + k * m->N;
+        }
+        MSF_TRY(msf_denoise_batch(cnns.data(), n, (msf_orient)(k - 1), vols.data(), in.data(), out.data(),
+                                  reinterpret_cast<void*>(st)));
+    }
+    for (int i = 0; i < n; ++i) MSF_TRY(enqueue_consensus(b->items[i], &prm[i], st));
+    return MSF_OK;
+}
+
+// Decides (outside any stream capture) whether the batch's CNN agents can share
+// launches: every problem runs the three CNN agents and every handle holds the
+// same parameters (compared on the host whenever a generation changed).
+static msf_status decide_shared(msf_mace_batch* b) {
+    const int n = (int)b->items.size();
+    std::vector<uint64_t> gens(n);
+    bool all_cnn = n <= 16;
+    for (int i = 0; i < n; ++i) {
+        const msf_mace_desc& d = b->items[i]->desc;
+        all_cnn = all_cnn && d.prior == MSF_PRIOR_CNN && d.K == 3;
+        gens[i] = cnn_generation(d.cnn);
+    }
+    if (!all_cnn) {
+        b->shared = false;
+        return MSF_OK;
+    }
+    if (gens == b->shared_gen) return MSF_OK;
+    const size_t np = msf_cnn_param_count();
+    std::vector<float> p0(np), pi(np);
+    MSF_TRY(msf_cnn_get_params(b->items[0]->desc.cnn, p0.data(), np));
+    bool same = true;
+    for (int i = 1; i < n && same; ++i) {
+        MSF_TRY(msf_cnn_get_params(b->items[i]->desc.cnn, pi.data(), np));
+        same = memcmp(p0.data(), pi.data(), np * sizeof(float)) == 0;
+    }
+    b->shared = same;
+    b->shared_gen = gens;
+    return MSF_OK;
+}
+
 // Fork: every problem stream waits for `st`; each enqueues its iteration; join.
 static msf_status enqueue_batch(msf_mace_batch* b, const msf_mace_params* prm, cudaStream_t st) {
+    if (b->shared) return enqueue_batch_shared(b, prm, st);
     const int n = (int)b->items.size();
     MSF_TRY_CUDA(cudaEventRecord(b->fork, st));
     for (int i = 0; i < n; ++i) {
@@ -447,10 +523,12 @@ extern "C" msf_status msf_mace_batch_step(msf_mace_batch* b, const msf_mace_para
     const int n = (int)b->items.size();
     for (int i = 0; i < n; ++i) MSF_TRY(check_params(b->items[i], &prm[i]));
     cudaStream_t st = as_stream(stream);
+    const bool was_shared = b->shared;
+    MSF_TRY(decide_shared(b));
     bool graph = true;
     for (int i = 0; i < n; ++i) graph = graph && prm[i].use_graph;
     if (graph) {
-        bool fresh = b->gexec != nullptr && (int)b->gprm.size() == n;
+        bool fresh = b->gexec != nullptr && (int)b->gprm.size() == n && was_shared == b->shared;
         for (int i = 0; fresh && i < n; ++i)
             fresh = same_params(b->gprm[i], prm[i]) && b->gcnn[i] == cnn_generation(b->items[i]->desc.cnn);
         if (!fresh) {

@@ -92,6 +92,8 @@ _SIGS = {
     "msf_cnn_set_params": (_I, [_P, _P, _Z]),
     "msf_cnn_get_params": (_I, [_P, _P, _Z]),
     "msf_denoise": (_I, [_P, _I, ctypes.POINTER(msf_vol), _P, _P, _P]),
+    "msf_denoise_batch": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(msf_vol), ctypes.POINTER(_P),
+                               ctypes.POINTER(_P), _P]),
     "msf_cnn_set_tuning": (_I, [_P, _I, ctypes.POINTER(msf_vol), _I, _I]),
     "msf_cnn_autotune": (_I, [_P, ctypes.POINTER(msf_vol), _P, _P, _P, ctypes.POINTER(_I)]),
     "msf_train_step": (_I, [_P, _P, _P, _I, _I, _I, _F, ctypes.POINTER(_F), _P]),
@@ -391,6 +393,16 @@ def msf_training_batch(vol_stack, vol: msf_vol, B: int, H: int, W: int, sigma_lo
 
 def msf_denoise(cnn: Cnn, orient: int, vol: msf_vol, x, out, stream=None):
     _check(lib().msf_denoise(cnn.handle, orient, ctypes.byref(vol), _f32(x), _f32(out), _stream(stream)))
+
+
+def msf_denoise_batch(cnns, orient: int, vols, xs, outs, stream=None):
+    """H_{orient,t} of several problems (one handle per problem, same parameters)."""
+    n = len(cnns)
+    hc = (ctypes.c_void_p * n)(*[c.handle.value for c in cnns])
+    hv = (msf_vol * n)(*vols)
+    hi = (ctypes.c_void_p * n)(*[_f32(x) for x in xs])
+    ho = (ctypes.c_void_p * n)(*[_f32(o) for o in outs])
+    _check(lib().msf_denoise_batch(hc, n, orient, hv, hi, ho, _stream(stream)))
 
 
 MSF_TILE_AUTO, MSF_TILE_16x8, MSF_TILE_PAIR = 0, 1, 2

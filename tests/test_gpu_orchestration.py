@@ -144,3 +144,60 @@ def test_every_launch_shape_gives_the_same_results(M):
         M.msf_projector_set_tuning(P, 128, 1, 16)
     with pytest.raises(M.MsfError):
         M.msf_projector_set_tuning(P, 32, 4, 12)
+
+
+def test_denoise_batch_equals_single_problems(M):
+    # uneven problems through the multi-problem persistent launches: (16^3 x 4),
+    # (24 x 32 x 40 x 6) and (32^3 x 3) run together; an odd height (21^3) and a
+    # handle too small for one chunk run on their own inside the same call
+    import torch
+    flat = M.pack_params(*synth.cnn_weights(97))
+    shapes = [(4, 16, 16, 16), (6, 24, 32, 40), (3, 21, 21, 21), (3, 32, 32, 32), (5, 16, 16, 16)]
+    small = [False, False, False, False, True]
+    cnns, vols, xs = [], [], []
+    for i, (sh, sm) in enumerate(zip(shapes, small)):
+        nt, nz, ny, nx = sh
+        c = M.Cnn(nz * ny * nx * (1 if sm else nt))
+        c.set_params(flat)
+        cnns.append(c)
+        vols.append(M.msf_vol(nx, ny, nz, nt, 1.0))
+        xs.append(torch.rand(sh, device="cuda", generator=torch.Generator("cuda").manual_seed(100 + i)))
+    for o in range(3):
+        outs = [torch.full_like(x, -5.0) for x in xs]
+        M.msf_denoise_batch(cnns, o, vols, xs, outs)
+        for c, v, x, out in zip(cnns, vols, xs, outs):
+            ref = torch.empty_like(x)
+            M.msf_denoise(c, o, v, x, ref)
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref), o
+
+
+def test_batch_with_shared_cnn_matches_individual_steps(M):
+    # every problem runs the three CNN agents with the same parameters: the
+    # batch takes the multi-problem path and must still equal the single steps
+    import torch
+    flat = M.pack_params(*synth.cnn_weights(98))
+    scans = [synth.Scan(n=16, nt=4, nu=24, nv=24, views=6),
+             synth.Scan(n=24, nt=5, nu=36, nv=28, views=9, mode="wedge90"),
+             synth.Scan(n=32, nt=3, nu=44, nv=36, views=12)]
+
+    def make(i, s):
+        q = _problem(M, s, 99 + i, M.MSF_PRIOR_CNN, flat)
+        q["m"].close()
+        q["cnn"].close()
+        q["cnn"] = M.Cnn(s.nt * s.n ** 3)        # room for every time-point
+        q["cnn"].set_params(flat)
+        q["m"] = M.Mace(q["P"], q["W"], q["X"], q["y"], q["lam"], M.MSF_PRIOR_CNN, cnn=q["cnn"])
+        return q
+
+    solo = [make(i, s) for i, s in enumerate(scans)]
+    batch = [make(i, s) for i, s in enumerate(scans)]
+    B = M.MaceBatch([q["m"] for q in batch])
+    for it in range(3):
+        graph = it > 0
+        res_solo = [M.msf_mace_step(q["m"], 0.8, 0.2, [0.25] * 4, 3) for q in solo]
+        res_b = M.msf_mace_batch_step(B, [_params(M, 4, graph=graph) for _ in batch])
+        assert res_solo == res_b, it
+    torch.cuda.synchronize()
+    for q, r in zip(solo, batch):
+        assert torch.equal(q["W"], r["W"]) and torch.equal(q["X"], r["X"])
