@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msf", choices=["msf", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "proj", "tiny", "batch", "sweep"])
+    ap.add_argument("--workload", default="full", choices=["full", "proj", "tiny", "batch", "sweep", "train"])
     ap.add_argument("--no-batch", action="store_true", help="skip the short uneven-batch measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -50,7 +50,8 @@ def parse():
 
 def workload(name):
     from paper_2008_01567_gb300 import synth
-    return {"full": synth.FULL, "proj": synth.PROJ, "tiny": synth.TINY, "batch": synth.FULL, "sweep": synth.PROJ}[name]
+    return {"full": synth.FULL, "proj": synth.PROJ, "tiny": synth.TINY, "batch": synth.FULL, "sweep": synth.PROJ,
+            "train": synth.FULL}[name]
 
 
 # settings of the plain and learned runs (rho, sigma and agent weights of Eq. (9)).
@@ -694,6 +695,63 @@ def extra_agents(P, prob, x_learned, x_plain, args):
     return out
 
 
+# ---------------------------------------------------------------- training workload
+
+def run_train(args, rank, world, dist, seed, peaks):
+    """--workload train: the CNN training step of Sec. V on its own (batch
+    128 x 5 x 64 x 64 patches, Adam), timed per step, with the per-kernel split
+    and the FLOP rate of its tensor-core kernels (forward, input and weight
+    gradients) against the measured BF16 peak."""
+    import torch
+    from paper_2008_01567_gb300 import msf, synth
+    ts = synth.Scan(n=128, nt=4, nu=8, nv=8, views=1)
+    Pt = msf.Projector(ts)
+    vols = torch.empty((ts.nt, 128, 128, 128), device="cuda")
+    msf.msf_phantom_voxelize(Pt.vol, synth.ellipsoids(seed + 101, 10, ts), vols, ss=2)
+    cnn = msf.Cnn(128 ** 3)
+    cnn.set_params(msf.pack_params(*synth.cnn_weights(seed + 102)))
+    TB, TH, TW = 128, 64, 64
+    cnn.train_reserve(TB * TH * TW)
+    tn = torch.empty((TB, 5, TH, TW), device="cuda")
+    tc_ = torch.empty((TB, TH, TW), device="cuda")
+    k = [0]
+
+    def step():
+        msf.msf_training_batch(vols, Pt.vol, TB, TH, TW, 0.02, 0.2, seed * 7919 + k[0], tn, tc_)
+        msf.msf_train_step(cnn, tn, tc_, 1e-3, want_loss=False)
+        k[0] += 1
+
+    for _ in range(args.warmup):
+        step()
+    msf.msf_profile_reset()
+    msf.msf_profile_enable(True)
+    ms = timed(step, args.steps, 0, dist)
+    msf.msf_profile_enable(False)
+    prof = msf.msf_profile_read()
+    P = TB * TH * TW
+    layer = 2.0 * 576 * 64 * P                       # one 64 -> 64 layer, one pass
+    flop = 3 * 8 * layer + 3 * 2.0 * 45 * 64 * P     # forward, input and weight gradients of the convs
+    tc_names = [n for n in prof if n.startswith("conv") or n.startswith("wgrad_tc")]
+    tc_ms = sum(prof[n][1] for n in tc_names) / args.steps
+    total_ms = sum(v[1] for v in prof.values()) / args.steps
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    if rank == 0:
+        line = {"metric": "CNN training steps/s (batch 128 x 5 x 64 x 64, Adam)", "value": world * args.steps / (ms / 1e3),
+                "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 (tensor cores), f32 (master weights, BatchNorm), f64 (sums)",
+                "data": "synthetic (seeded moving-ellipsoid phantom patches, Gaussian noise U[0.02, 0.2])",
+                "config": {"workload": "training step of the 2.5D CNN, 10 layers, 64 channels, batch 128 x 64 x 64"},
+                "tensor_kernels": {"names": sorted(tc_names), "ms_per_step": tc_ms,
+                                   "tflops": flop / (tc_ms / 1e3) / 1e12,
+                                   "frac_of_bf16_peak": flop / (tc_ms / 1e3) / 1e12 / peak if peak else None},
+                "flop_per_step": flop, "kernel_ms_per_step": total_ms,
+                "kernels": {n: {"launches": v[0], "ms": round(v[1], 3)} for n, v in
+                            sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+        print(json.dumps(line))
+    return None
+
+
 # ---------------------------------------------------------------- main
 
 def main():
@@ -736,6 +794,8 @@ def main():
     seed = replica_seed(rank)
     if args.workload == "batch":
         return run_batch(args, rank, world, dist, seed)
+    if args.workload == "train":
+        return run_train(args, rank, world, dist, seed, peaks)
     if args.workload == "sweep":
         return run_sweep(args, rank, world, dist, seed)
     prob = make_problem(scan, seed)

@@ -2700,13 +2700,17 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     const int nred = w.nred;
     auto reduce = [&](int mode, const void* t0, const float* t1, const float* bnp, const float* ga,
                       const float* be, double* out) -> msf_status {
-        MSF_PROF("train_reduce", st);
-        if (mode == RED_MOMENTS)
-            channel_reduce_kernel<RED_MOMENTS><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
-        else if (mode == RED_BNBWD)
-            channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
-        else
-            channel_reduce_kernel<RED_SUM><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+        {
+            MSF_PROF("train_reduce", st);
+            if (mode == RED_MOMENTS)
+                channel_reduce_kernel<RED_MOMENTS><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+            else if (mode == RED_BNBWD)
+                channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+            else
+                channel_reduce_kernel<RED_SUM><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+            MSF_LAUNCH_CHECK();
+        }
+        MSF_PROF("train_reduce_finalize", st);
         channel_finalize_kernel<<<1, 128, 0, st>>>(w.part, nred, out);
         MSF_LAUNCH_CHECK();
         return MSF_OK;
@@ -2725,8 +2729,12 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
         MSF_TRY(reduce(RED_MOMENTS, w.z[l], nullptr, nullptr, nullptr, nullptr, sums));
         {
-            MSF_PROF("train_bn", st);
+            MSF_PROF("train_bn_stats", st);
             bn_stats_kernel<<<1, CH, 0, st>>>(sums, bnp, c->d_params + o.mean[l], c->d_params + o.var[l], (double)P);
+            MSF_LAUNCH_CHECK();
+        }
+        {
+            MSF_PROF("train_bn_apply", st);
             bn_apply_relu_kernel<<<152 * 8, 256, 0, st>>>(w.z[l], (uint4*)w.act[l + 1], bnp,
                                                           c->d_params + o.gamma[l], c->d_params + o.beta[l], n8);
             MSF_LAUNCH_CHECK();
@@ -2758,10 +2766,14 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         const float* be = c->d_params + o.beta[l];
         MSF_TRY(reduce(RED_BNBWD, w.g[cur], w.z[l], bnp, ga, be, sums + 2 * CH));
         {
-            MSF_PROF("train_bn_bwd", st);
+            MSF_PROF("train_copy_grads", st);
             // d gamma = sum dy xhat, d beta = sum dy
             copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums + 3 * CH, c->d_grad + o.gamma[l], CH);
             copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums + 2 * CH, c->d_grad + o.beta[l], CH);
+            MSF_LAUNCH_CHECK();
+        }
+        {
+            MSF_PROF("train_bn_bwd", st);
             bn_bwd_apply_kernel<<<152 * 8, 256, 0, st>>>((const uint4*)w.g[cur], w.z[l],
                                                          (uint4*)w.g[cur ^ 1], bnp, ga, be, sums + 2 * CH, (double)P, n8);
             MSF_LAUNCH_CHECK();
@@ -2770,7 +2782,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         // dz in g[cur ^ 1]: conv bias grad, weight grad, input grad
         MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, sums));
         {
-            MSF_PROF("train_wgrad", st);
+            MSF_PROF("train_copy_grads", st);
             copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums, c->d_grad + o.b[l], CH);
             MSF_LAUNCH_CHECK();
         }
