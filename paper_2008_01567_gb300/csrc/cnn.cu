@@ -2159,26 +2159,42 @@ __global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restr
             be[i] = beta[lane8 * 8 + i];
         }
     }
-    for (size_t p = blockIdx.x * (size_t)32 + row; p < P; p += (size_t)gridDim.x * 32) {
-        float a[8];
-        if (MODE == RED_MOMENTS) f32x8_load(static_cast<const float*>(t0v) + p * CH + lane8 * 8, a);
-        else bf16x8_to_f32(static_cast<const uint4*>(t0v)[p * 8 + lane8], a);
-        if (MODE == RED_MOMENTS) {
+    // Each thread sums runs of RED_RUN of its pixels in FP32 and adds each run
+    // into its FP64 sums (FP64 arithmetic is a small fraction of the FP32 rate
+    // on this GPU); the order of every addition is fixed.
+    constexpr int RED_RUN = 8;
+    const size_t stride = (size_t)gridDim.x * 32;
+    size_t p = blockIdx.x * (size_t)32 + row;
+    while (p < P) {
+        float r0[8], r1[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) { s0[i] += a[i]; s1[i] += (double)a[i] * a[i]; }
-        } else if (MODE == RED_SUM) {
+        for (int i = 0; i < 8; ++i) r0[i] = r1[i] = 0.0f;
+        for (int k = 0; k < RED_RUN && p < P; ++k, p += stride) {
+            float a[8];
+            if (MODE == RED_MOMENTS) f32x8_load(static_cast<const float*>(t0v) + p * CH + lane8 * 8, a);
+            else bf16x8_to_f32(static_cast<const uint4*>(t0v)[p * 8 + lane8], a);
+            if (MODE == RED_MOMENTS) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) s0[i] += a[i];
-        } else {
-            float z[8];
-            f32x8_load(t1 + p * CH + lane8 * 8, z);
+                for (int i = 0; i < 8; ++i) { r0[i] += a[i]; r1[i] = fmaf(a[i], a[i], r1[i]); }
+            } else if (MODE == RED_SUM) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float xh = (z[i] - mean[i]) * istd[i];
-                const float dy = (ga[i] * xh + be[i] > 0.0f) ? a[i] : 0.0f;
-                s0[i] += dy;
-                s1[i] += (double)dy * xh;
+                for (int i = 0; i < 8; ++i) r0[i] += a[i];
+            } else {
+                float z[8];
+                f32x8_load(t1 + p * CH + lane8 * 8, z);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float xh = (z[i] - mean[i]) * istd[i];
+                    const float dy = (ga[i] * xh + be[i] > 0.0f) ? a[i] : 0.0f;
+                    r0[i] += dy;
+                    r1[i] = fmaf(dy, xh, r1[i]);
+                }
             }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            s0[i] += (double)r0[i];
+            s1[i] += (double)r1[i];
         }
     }
 #pragma unroll
@@ -2231,10 +2247,24 @@ __global__ void bn_apply_relu_kernel(const float* __restrict__ z, uint4* __restr
 }
 
 // dz = gamma istd (dy - sum(dy)/P - xhat sum(dy xhat)/P), dy = g [y > 0].
-__global__ void bn_bwd_apply_kernel(const uint4* __restrict__ g, const float* __restrict__ z, uint4* __restrict__ dz,
-                                    const float* __restrict__ bnp, const float* __restrict__ gamma,
-                                    const float* __restrict__ beta, const double* __restrict__ sums, double P,
-                                    size_t n8) {
+// The per-channel factors are formed once per block (the two FP64 means
+// rounded to FP32, as the element loop used them); the element loop is FP32.
+__global__ void __launch_bounds__(256) bn_bwd_apply_kernel(const uint4* __restrict__ g, const float* __restrict__ z,
+                                                           uint4* __restrict__ dz, const float* __restrict__ bnp,
+                                                           const float* __restrict__ gamma,
+                                                           const float* __restrict__ beta,
+                                                           const double* __restrict__ sums, double P, size_t n8) {
+    __shared__ float s_mean[CH], s_istd[CH], s_g[CH], s_b[CH], s_m1[CH], s_m2[CH];
+    if (threadIdx.x < CH) {
+        const int c = threadIdx.x;
+        s_mean[c] = bnp[c];
+        s_istd[c] = bnp[CH + c];
+        s_g[c] = gamma[c];
+        s_b[c] = beta[c];
+        s_m1[c] = (float)(sums[c] / P);
+        s_m2[c] = (float)(sums[CH + c] / P);
+    }
+    __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
         const int c0 = (int)(i & 7) * 8;
         float gv[8], zv[8], o[8];
@@ -2243,10 +2273,9 @@ __global__ void bn_bwd_apply_kernel(const uint4* __restrict__ g, const float* __
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int c = c0 + k;
-            const float xh = (zv[k] - bnp[c]) * bnp[CH + c];
-            const float dy = (gamma[c] * xh + beta[c] > 0.0f) ? gv[k] : 0.0f;
-            const float m1 = (float)(sums[c] / P), m2 = (float)(sums[CH + c] / P);
-            o[k] = gamma[c] * bnp[CH + c] * (dy - m1 - xh * m2);
+            const float xh = (zv[k] - s_mean[c]) * s_istd[c];
+            const float dy = (s_g[c] * xh + s_b[c] > 0.0f) ? gv[k] : 0.0f;
+            o[k] = s_g[c] * s_istd[c] * (dy - s_m1[c] - xh * s_m2[c]);
         }
         dz[i] = f32_to_bf16x8(o);
     }
