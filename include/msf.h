@@ -456,6 +456,15 @@ void msf_mace_destroy(msf_mace* m);
  * change.  Results are identical to the eager path. */
 msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, double* h_residual, void* stream);
 
+/* New measurements for a MACE problem from host memory: copies the photon
+ * counts h_counts (host, [nt][views][nv][nu] FP32; pinned memory makes the
+ * copy asynchronous) into the handle and forms y = -ln(max(n,1)/I0) and
+ * Lambda = c exp(-y) there (msf_weights); from then on the handle's steps use
+ * these instead of desc.d_y and desc.d_lambda.  The first call allocates three
+ * sinograms in the handle (outside any stream capture) and drops a captured
+ * iteration; later calls allocate nothing.  Ordered on `stream`. */
+msf_status msf_mace_set_counts(msf_mace* m, const float* h_counts, double I0, double c, void* stream);
+
 /* The consensus and Mann update of Algorithm 1 alone (Sec. III, Eqs. (8), (9),
  * (12)): W_i <- W_i + 2 rho (sum_j mu_j (2 X_j - W_j) - X_i) on caller-owned
  * stacks d_W, d_X of K1 = K + 1 states of N voxels each ([K1][N], FP32, K1 = 2

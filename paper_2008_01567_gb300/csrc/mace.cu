@@ -23,6 +23,7 @@ struct msf_mace {
     double* d_sums = nullptr;      // [2]
     double* h_sums = nullptr;      // pinned [2], written by the step's last copy
     int* h_status = nullptr;       // pinned copy of the data agent's numeric status word
+    float* d_meas = nullptr;       // msf_mace_set_counts: counts, y, Lambda (3 sinograms)
     int nblocks = 0;
     size_t N = 0;                  // voxels of one 4D volume
     // with the q-GGMRF prior the data agent and the prior agent run on two
@@ -446,6 +447,7 @@ extern "C" void msf_mace_destroy(msf_mace* m) {
     cudaFree(m->d_sums);
     if (m->h_sums) cudaFreeHost(m->h_sums);
     if (m->h_status) cudaFreeHost(m->h_status);
+    cudaFree(m->d_meas);
     delete m;
 }
 
@@ -473,6 +475,25 @@ extern "C" msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, dou
         MSF_TRY(read_residual(m, h_residual));
     }
     return MSF_OK;
+}
+
+extern "C" msf_status msf_mace_set_counts(msf_mace* m, const float* h_counts, double I0, double c, void* stream) {
+    MSF_REQUIRE(m && h_counts, "msf_mace_set_counts: NULL argument");
+    MSF_REQUIRE(I0 > 0 && c > 0 && isfinite(I0) && isfinite(c), "msf_mace_set_counts: I0 and c must be positive");
+    const size_t M = projector_sino_size(m->desc.proj);
+    cudaStream_t st = as_stream(stream);
+    if (!m->d_meas) {
+        if (cudaMalloc(&m->d_meas, 3 * M * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            m->d_meas = nullptr;
+            return fail(MSF_ERR_NOMEM, "msf_mace_set_counts: out of device memory");
+        }
+        m->desc.d_y = m->d_meas + M;
+        m->desc.d_lambda = m->d_meas + 2 * M;
+        drop_graph(m->gexec);   // a captured iteration read the caller's buffers
+    }
+    MSF_TRY_CUDA(cudaMemcpyAsync(m->d_meas, h_counts, M * sizeof(float), cudaMemcpyHostToDevice, st));
+    return msf_weights(m->d_meas, m->d_meas + M, m->d_meas + 2 * M, M, I0, c, stream);
 }
 
 extern "C" msf_status msf_mace_batch_create(msf_mace** problems, int n, msf_mace_batch** out) {

@@ -105,6 +105,7 @@ _SIGS = {
     "msf_mace_create": (_I, [ctypes.POINTER(msf_mace_desc), ctypes.POINTER(_P)]),
     "msf_mace_destroy": (None, [_P]),
     "msf_mace_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
+    "msf_mace_set_counts": (_I, [_P, _P, _D, _D, _P]),
     "msf_mace_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     "msf_mace_batch_destroy": (None, [_P]),
     "msf_mace_batch_step": (_I, [_P, ctypes.POINTER(msf_mace_params), ctypes.POINTER(_D), _P]),
@@ -500,6 +501,15 @@ def msf_mace_step(m: Mace, rho: float, sigma: float, mu, n_cg: int, n_sweeps: in
     _check(lib().msf_mace_step(m.handle, ctypes.byref(prm), ctypes.byref(r) if want_residual else None,
                                _stream(stream)))
     return r.value if want_residual else None
+
+
+def msf_mace_set_counts(m: Mace, counts_host, I0: float, c: float, stream=None):
+    """New photon counts for the problem from a host tensor (float32, contiguous;
+    pinned memory keeps the copy asynchronous)."""
+    import torch
+    if counts_host.is_cuda or counts_host.dtype != torch.float32 or not counts_host.is_contiguous():
+        raise ValueError("expected a contiguous float32 host tensor")
+    _check(lib().msf_mace_set_counts(m.handle, counts_host.data_ptr(), I0, c, _stream(stream)))
 
 
 def msf_mace_consensus(W, X, mu, rho: float, work, stream=None):

@@ -231,3 +231,30 @@ def test_learned_prior_beats_plain_prior(M):
         plain[sx] = nrmse(X2[0])
     print(f"NRMSE learned {learned:.4f}  plain {plain}")
     assert learned <= min(plain.values())
+
+
+def test_counts_from_host_memory_give_the_same_steps(M):
+    # msf_mace_set_counts (host counts -> y, Lambda inside the handle) against
+    # the same counts conditioned by msf_weights on the device: identical steps
+    import torch
+    scan = synth.TINY
+    x0, counts, y, lam = measurement(scan, 71)
+    P1, P2 = M.Projector(scan), M.Projector(scan)
+    c_dev = torch.from_numpy(counts.astype(np.float32)).cuda()
+    yg, lg = torch.empty_like(c_dev), torch.empty_like(c_dev)
+    M.msf_weights(c_dev, yg, lg, I0, I0)
+    shape = (2, scan.nt, scan.n, scan.n, scan.n)
+    Wa, Xa = torch.zeros(shape, device="cuda"), torch.zeros(shape, device="cuda")
+    Wb, Xb = torch.zeros(shape, device="cuda"), torch.zeros(shape, device="cuda")
+    mrf = M.msf_mrf(2.0, 1.2, 1.0, 0.2, 0.5)
+    ma = M.Mace(P1, Wa, Xa, yg, lg, M.MSF_PRIOR_QGGMRF, mrf=mrf)
+    zeros = torch.zeros_like(c_dev)                      # the handle's own data replaces these
+    mb = M.Mace(P2, Wb, Xb, zeros, zeros, M.MSF_PRIOR_QGGMRF, mrf=mrf)
+    h = torch.from_numpy(counts.astype(np.float32)).pin_memory()
+    for it in range(3):
+        M.msf_mace_set_counts(mb, h, I0, I0)
+        ra = M.msf_mace_step(ma, 0.5, 0.1, [0.5, 0.5], 3, 1, use_graph=it > 0)
+        rb = M.msf_mace_step(mb, 0.5, 0.1, [0.5, 0.5], 3, 1, use_graph=it > 0)
+        assert ra == rb
+    torch.cuda.synchronize()
+    assert torch.equal(Xa, Xb) and torch.equal(Wa, Wb)
