@@ -519,7 +519,10 @@ __global__ void cg_finalize_kernel(const double* __restrict__ partial, int npart
     }
 }
 
-// z += alpha p; r -= alpha q; partial r.r  (grid: blocks_per_frame x nt)
+// z += alpha p; r -= alpha q; partial r.r  (grid: blocks_per_frame x nt).
+// Each thread adds the squares of runs of 8 of its elements in FP32 before its
+// FP64 sum (FP64 arithmetic is a small fraction of the FP32 rate on this GPU);
+// the order of every addition is fixed.
 __global__ void cg_update_kernel(float* __restrict__ z, float* __restrict__ r,
                                  const float* __restrict__ p, const float* __restrict__ q,
                                  const double* __restrict__ alpha, double* __restrict__ partial,
@@ -527,13 +530,18 @@ __global__ void cg_update_kernel(float* __restrict__ z, float* __restrict__ r,
     const int t = blockIdx.y;
     const float a = (float)alpha[t];
     const size_t off = (size_t)t * fs;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
     double dot = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < fs;
-         i += (size_t)gridDim.x * blockDim.x) {
-        z[off + i] = __fmaf_rn(a, p[off + i], z[off + i]);
-        const float rn = __fmaf_rn(-a, q[off + i], r[off + i]);
-        r[off + i] = rn;
-        dot += (double)rn * (double)rn;
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    while (i < fs) {
+        float run = 0.0f;
+        for (int k = 0; k < 8 && i < fs; ++k, i += stride) {
+            z[off + i] = __fmaf_rn(a, p[off + i], z[off + i]);
+            const float rn = __fmaf_rn(-a, q[off + i], r[off + i]);
+            r[off + i] = rn;
+            run = __fmaf_rn(rn, rn, run);
+        }
+        dot += (double)run;
     }
     const double s = block_sum_f64(dot);
     if (threadIdx.x == 0) partial[(size_t)t * gridDim.x + blockIdx.x] = s;
