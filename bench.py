@@ -337,6 +337,60 @@ def cpu_baseline(scan, settings, learned: bool):
             "ms_per_iter": T * 1e3}
 
 
+# ---------------------------------------------------------------- the tiny workload end to end
+
+TINY_RUN = dict(rho=0.5, sigma=0.1, mu=[0.5, 0.5], n_cg=5, n_sweeps=1, sx=0.2, q=1.2, T=1.0, bt=0.5, iters=10)
+
+
+def tiny_gpu(seed):
+    """The plain method on the tiny workload (24^3 x 4, 32 x 32 detector, 12
+    views, 3 ellipsoids): 10 MACE iterations from zero, timed from the photon
+    counts on; returns the rate, X_0 and the counts (for the oracle leg)."""
+    import torch
+    from paper_2008_01567_gb300 import msf, synth
+    sc = synth.TINY
+    P = msf.Projector(sc)
+    ell = synth.ellipsoids(seed + 7, 3, sc)
+    p = torch.empty((sc.nt, sc.views, sc.nv, sc.nu), device="cuda")
+    msf.msf_phantom_project(P, ell, p)
+    counts = synth.poisson(seed + 8, I0 * np.exp(-p.cpu().numpy().astype(np.float64))).astype(np.float32)
+    c = torch.from_numpy(counts).cuda()
+    y, lam = torch.empty_like(c), torch.empty_like(c)
+    R = TINY_RUN
+    shape = (2, sc.nt, sc.n, sc.n, sc.n)
+    W, X = torch.zeros(shape, device="cuda"), torch.zeros(shape, device="cuda")
+    m = msf.Mace(P, W, X, y, lam, msf.MSF_PRIOR_QGGMRF, mrf=msf.msf_mrf(2.0, R["q"], R["T"], R["sx"], R["bt"]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    msf.msf_weights(c, y, lam, I0, I0)
+    for _ in range(R["iters"]):
+        msf.msf_mace_step(m, R["rho"], R["sigma"], R["mu"], R["n_cg"], R["n_sweeps"], want_residual=False)
+    x0 = X[0].cpu().numpy()
+    dt = time.perf_counter() - t0
+    m.close()
+    return {"iters_per_s": R["iters"] / dt}, x0, counts
+
+
+def tiny_oracle(counts, x_gpu):
+    """The same 10 iterations in the FP64 oracle on the host cores, from the
+    same counts; rate and the relative L2 distance of the GPU's X_0 from it."""
+    import oracle
+    from paper_2008_01567_gb300 import synth
+    oracle.build()
+    sc = synth.TINY
+    R = TINY_RUN
+    c64 = counts.astype(np.float64)
+    t0 = time.perf_counter()
+    y = oracle.log_measurement(c64, I0)
+    lam = oracle.weights(y, I0)
+    agents = [lambda w, x: oracle.prox_data(y, lam, w, x, sc, R["sigma"], R["n_cg"]),
+              lambda w, x: oracle.prox_qggmrf(w, x, R["sigma"], 2.0, R["q"], R["T"], R["sx"], R["bt"], R["n_sweeps"])]
+    xhat, _, _, _ = oracle.mace(np.zeros((sc.nt, sc.n, sc.n, sc.n)), agents, R["mu"], R["rho"], R["iters"])
+    dt = time.perf_counter() - t0
+    rel = float(np.linalg.norm(x_gpu.astype(np.float64) - xhat) / np.linalg.norm(xhat))
+    return {"iters_per_s": R["iters"] / dt, "cores": len(os.sched_getaffinity(0)), "rel_l2_gpu_vs_oracle": rel}
+
+
 # ---------------------------------------------------------------- the queue of uneven problems
 
 def make_batch(params, seed, learned):
@@ -914,10 +968,14 @@ def main():
     adj_ms = pp["joseph_adj"][1] / pp["joseph_adj"][0]
     projector = projector_roofline(scan, fwd_ms, adj_ms, ck.get("sm_mhz"), peaks)
 
+    tiny_rate, tiny_x, tiny_counts = tiny_gpu(seed)
+    tiny = {"workload": "plain MACE 24^3x4, det 32x32, 12 views/frame, 10 iterations from the counts",
+            "gpu": tiny_rate}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(scan, L, learned=True)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        tiny["oracle"] = tiny_oracle(tiny_counts, tiny_x)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MACE iters/s", "n_gpus": world, "steps": args.steps,
@@ -934,6 +992,7 @@ def main():
                 "learned_vs_plain": {"iters": args.iters,
                                      "nrmse_learned": q_learned["nrmse"], "nrmse_plain": q_plain["nrmse"],
                                      "learned_not_worse": q_learned["nrmse"] <= q_plain["nrmse"]},
+                "tiny_end_to_end": tiny,
                 "training": training, "conv_tuning": {str(k): list(v) for k, v in conv_tuning.items()},
                 "projector": projector, **extra,
                 "projector_tuning": {"fwd_block": list(tuned[:2]), "adj_zrun": tuned[2]}, "batch": batch,
