@@ -579,9 +579,10 @@ def quality_run(step, X0, x_true, iters, points=QUALITY_POINTS):
     """Runs `step` (one MACE iteration returning the consensus residual) from the
     state it is given (W = X = 0) for max(iters, points) iterations, untimed and
     separate from the throughput measurements.  Records NRMSE of X_0 and the
-    residual at every point, and NRMSE / PSNR / SSIM at exactly `iters`."""
+    residual at every point up to 2 * iters, and NRMSE / PSNR / SSIM at exactly
+    `iters`."""
     from paper_2008_01567_gb300 import metrics
-    pts = sorted(set(p for p in points) | {iters})
+    pts = sorted(set(p for p in points if p <= 2 * iters) | {iters})
     traj, at = [], None
     for it in range(1, pts[-1] + 1):
         res = step(want_residual=it in pts)
