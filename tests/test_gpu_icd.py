@@ -113,3 +113,23 @@ def test_mace_with_icd_data_agent_matches_oracle(M):
               lambda w, x: oracle.prox_qggmrf(w, x, sigma, 2.0, 1.2, 1.0, 0.2, 0.5, n_sw)]
     xhat, _, _, _ = oracle.mace(np.zeros(shape[1:]), agents, mu, rho, iters)
     assert rel_l2(X[0].cpu().numpy(), xhat) <= 1e-3
+
+
+def test_mace_with_icd_graph_equals_eager(M):
+    # the ICD data agent inside a captured MACE iteration: same bits as eager
+    import torch
+    scan = synth.TINY
+    x0, y, lam, P1, dp, yg, lg = _setup(M, scan, 46)
+    P2 = M.Projector(scan)
+    shape = (2, scan.nt, scan.n, scan.n, scan.n)
+    mrf = M.msf_mrf(2.0, 1.2, 1.0, 0.2, 0.5)
+    Wa, Xa = torch.zeros(shape, device="cuda"), torch.zeros(shape, device="cuda")
+    Wb, Xb = torch.zeros(shape, device="cuda"), torch.zeros(shape, device="cuda")
+    ma = M.Mace(P1, Wa, Xa, yg, lg, M.MSF_PRIOR_QGGMRF, mrf=mrf)
+    mb = M.Mace(P2, Wb, Xb, yg, lg, M.MSF_PRIOR_QGGMRF, mrf=mrf)
+    for it in range(3):
+        ra = M.msf_mace_step(ma, 0.5, 0.1, [0.5, 0.5], 0, 1, n_icd=2)
+        rb = M.msf_mace_step(mb, 0.5, 0.1, [0.5, 0.5], 0, 1, n_icd=2, use_graph=True)
+        assert ra == rb
+    torch.cuda.synchronize()
+    assert torch.equal(Xa, Xb) and torch.equal(Wa, Wb)
