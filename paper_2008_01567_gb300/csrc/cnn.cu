@@ -1226,13 +1226,21 @@ static_assert(wg_win(wg_hi(0)) > wg_win(wg_lo(0)) && wg_win(wg_hi(1)) > wg_win(w
                   wg_win(wg_hi(4)) > wg_win(wg_lo(4)),
               "the second tap of an MMA pair must lie above the first (positive leading byte offset)");
 
+// TAPS = 1 is the first layer on its packed 5 x 3 x 3 neighbourhoods (no halo):
+// one act box and the dz box per tile, and one MMA per K-step whose second 64
+// rows of A are the dz box (dropped), so D[k][co] comes out in rows 0-63.
+template <int TAPS>
 __global__ void __launch_bounds__(THREADS, 1)
 wgrad_tc_kernel(const __grid_constant__ CUtensorMap map_act, const __grid_constant__ CUtensorMap map_dz,
                 float* __restrict__ part, TileGeom tg, int* __restrict__ err) {
+    static_assert(TAPS == 9 || TAPS == 1, "3x3 hidden layers or the packed first layer");
+    constexpr int SB = TAPS == 9 ? WG_STAGE_BYTES : 2 * TILE_BYTES;     // stage bytes
+    constexpr int DZ_OFF = TAPS == 9 ? 3 * HALO_BYTES : TILE_BYTES;      // the dz box inside a stage
+    constexpr int NG = TAPS == 9 ? 5 : 1;                                // MMAs per K-step
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sS = smem;
-    uint64_t* bars = (uint64_t*)(sS + WG_STAGES * WG_STAGE_BYTES + WG_SLACK);
+    uint64_t* bars = (uint64_t*)(sS + WG_STAGES * SB + WG_SLACK);
     uint64_t* full = bars;
     uint64_t* empty = bars + WG_STAGES;
     uint64_t* done = bars + 2 * WG_STAGES;
@@ -1276,12 +1284,16 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap map_act, const __grid_consta
                 }
                 int img, a0, b0;
                 decode_tile(tg, tile, img, a0, b0);
-                uint8_t* dst = sS + s * WG_STAGE_BYTES;
-                tc::mbar_expect_tx(&full[s], WG_STAGE_BYTES);
+                uint8_t* dst = sS + s * SB;
+                tc::mbar_expect_tx(&full[s], SB);
+                if (TAPS == 9) {
 #pragma unroll
-                for (int bx = 0; bx < 3; ++bx)
-                    tc::tma_load_4d(dst + bx * HALO_BYTES, &map_act, &full[s], 0, b0 + bx - 1, a0 - 1, img);
-                tc::tma_load_4d(dst + 3 * HALO_BYTES, &map_dz, &full[s], 0, b0, a0, img);
+                    for (int bx = 0; bx < 3; ++bx)
+                        tc::tma_load_4d(dst + bx * HALO_BYTES, &map_act, &full[s], 0, b0 + bx - 1, a0 - 1, img);
+                } else {
+                    tc::tma_load_4d(dst, &map_act, &full[s], 0, b0, a0, img);
+                }
+                tc::tma_load_4d(dst + DZ_OFF, &map_dz, &full[s], 0, b0, a0, img);
                 issued[s] = u + 1;
             }
             if (!ok) {
@@ -1303,15 +1315,21 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap map_act, const __grid_consta
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t st_base = tc::smem_u32(sS + s * WG_STAGE_BYTES);
+                const uint32_t st_base = tc::smem_u32(sS + s * SB);
 #pragma unroll
                 for (int k = 0; k < TILE_A / 2; ++k) {
-                    const uint64_t bd = tc::desc_sw128_mn(st_base + 3 * HALO_BYTES + k * 2048, 1024);
+                    const uint64_t bd = tc::desc_sw128_mn(st_base + DZ_OFF + k * 2048, 1024);
+                    if (TAPS == 9) {
 #pragma unroll
-                    for (int g = 0; g < 5; ++g) {
-                        const uint32_t lo = st_base + wg_win(wg_lo(g)) + k * 2048;
-                        const uint64_t ad = tc::desc_sw128_mn(lo, (uint32_t)(wg_win(wg_hi(g)) - wg_win(wg_lo(g))));
-                        tc::mma_bf16(tmem_base + g * 64, ad, bd, idesc, (j | k) ? 1u : 0u);
+                        for (int g = 0; g < NG; ++g) {
+                            const uint32_t lo = st_base + wg_win(wg_lo(g)) + k * 2048;
+                            const uint64_t ad =
+                                tc::desc_sw128_mn(lo, (uint32_t)(wg_win(wg_hi(g)) - wg_win(wg_lo(g))));
+                            tc::mma_bf16(tmem_base + g * 64, ad, bd, idesc, (j | k) ? 1u : 0u);
+                        }
+                    } else {
+                        const uint64_t ad = tc::desc_sw128_mn(st_base + k * 2048, (uint32_t)DZ_OFF);
+                        tc::mma_bf16(tmem_base, ad, bd, idesc, (j | k) ? 1u : 0u);
                     }
                 }
                 tc::mma_commit(&empty[s]);
@@ -1327,14 +1345,16 @@ wgrad_tc_kernel(const __grid_constant__ CUtensorMap map_act, const __grid_consta
             tc::fence_after_sync();
             float* out = part + (size_t)blockIdx.x * 9 * CH * CH;
 #pragma unroll 1
-            for (int g = 0; g < 5; ++g) {
-                if (g == 4 && q < 2) continue;   // tap 7 again: dropped (warp-uniform)
+            for (int g = 0; g < NG; ++g) {
+                // the dropped halves (warp-uniform): tap 7 again, or the first
+                // layer's dz rows
+                if ((TAPS == 9 && g == 4 && q < 2) || (TAPS == 1 && q >= 2)) continue;
                 uint32_t r[64];
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + g * 64;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) tc::tmem_ld16(taddr + c * 16, r + c * 16);
                 tc::tmem_ld_wait();
-                const int tap = m < 64 ? wg_lo(g) : wg_hi(g), ci = m & 63;
+                const int tap = TAPS == 1 ? 0 : (m < 64 ? wg_lo(g) : wg_hi(g)), ci = m & 63;
                 float* o = out + (size_t)tap * CH * CH + ci;
 #pragma unroll
                 for (int co = 0; co < CH; ++co) o[co * CH] = __uint_as_float(r[co]);
@@ -1483,7 +1503,8 @@ static msf_status ensure_kernel_attrs() {
                                       C1Cfg::SMEM));
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_kernel<EPI_PART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairCfg::SMEM));
-    MSF_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
+    MSF_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM));
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_multi_kernel<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       PairCfg::SMEM));
     MSF_TRY_CUDA(cudaFuncSetAttribute(conv_pair_multi_kernel<EPI_PART>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2005,8 +2026,9 @@ extern "C" msf_status msf_cnn_autotune(msf_cnn* c, const msf_vol* vol, const flo
 //                  hidden layers with EPI_RAW, last layer with EPI_F32)
 //   input grads:   tcgen05 with the transposed, flipped kernels
 //                  W'[tap'][ci][co] = W[co][ci][2-ky][2-kx]
-//   weight grads:  FP32 SIMT reduction over pixels, split into chunks and
-//                  summed in a fixed order.
+//   weight grads:  tcgen05 (wgrad_tc_kernel: MN-major operands, per-CTA TMEM
+//                  accumulation, CTA partials summed in a fixed order); the
+//                  64 -> 1 output layer's in FP32 SIMT
 
 namespace msf {
 namespace cnn {
@@ -2361,64 +2383,6 @@ __global__ void last_dgrad_kernel(const float* __restrict__ dR, const float* __r
             da[p * 8 + c8] = f32_to_bf16x8(o);
         }
     }
-}
-
-// Weight-gradient partials of a 64 -> 64 (TAPS = 9) or packed (TAPS = 1)
-// layer over one chunk of pixels:
-//   part[chunk][tap][co][ci] = sum_p dz[p][co] * act[p + off(tap)][ci]
-// 256 threads, each a 4 x 4 block of (co, ci); pixels staged 32 at a time.
-template <int TAPS>
-__global__ void __launch_bounds__(256) wgrad_kernel(const uint4* __restrict__ dz, const uint4* __restrict__ act,
-                                                    float* __restrict__ part, int B, int H, int W) {
-    __shared__ __align__(16) float sd[32][CH];
-    __shared__ __align__(16) float sa[32][CH];
-    const int tap = blockIdx.x, chunk = blockIdx.y;
-    const int dy = TAPS == 9 ? tap / 3 - 1 : 0, dx = TAPS == 9 ? tap % 3 - 1 : 0;
-    const size_t P = (size_t)B * H * W;
-    const size_t p_lo = (size_t)chunk * WG_CHUNK;
-    const size_t p_hi = p_lo + WG_CHUNK < P ? p_lo + WG_CHUNK : P;
-    const int co4 = (threadIdx.x >> 4) * 4, ci4 = (threadIdx.x & 15) * 4;
-    float acc[4][4] = {};
-    const int lr = threadIdx.x >> 3, lc = threadIdx.x & 7;     // loader: pixel row, 8-channel group
-    for (size_t p0 = p_lo; p0 < p_hi; p0 += 32) {
-        const size_t p = p0 + lr;
-        float v[8], u[8];
-        if (p < p_hi) {
-            bf16x8_to_f32(dz[p * 8 + lc], v);
-            const int b = (int)(p % W), a = (int)((p / W) % H);
-            const int aa = a + dy, bb = b + dx;
-            if (aa >= 0 && aa < H && bb >= 0 && bb < W) {
-                bf16x8_to_f32(act[(p + (ptrdiff_t)dy * W + dx) * 8 + lc], u);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) u[k] = 0.0f;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = u[k] = 0.0f;
-        }
-        *reinterpret_cast<float4*>(&sd[lr][lc * 8]) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4*>(&sd[lr][lc * 8 + 4]) = make_float4(v[4], v[5], v[6], v[7]);
-        *reinterpret_cast<float4*>(&sa[lr][lc * 8]) = make_float4(u[0], u[1], u[2], u[3]);
-        *reinterpret_cast<float4*>(&sa[lr][lc * 8 + 4]) = make_float4(u[4], u[5], u[6], u[7]);
-        __syncthreads();
-#pragma unroll 8
-        for (int j = 0; j < 32; ++j) {
-            const float4 d = *reinterpret_cast<const float4*>(&sd[j][co4]);
-            const float4 x = *reinterpret_cast<const float4*>(&sa[j][ci4]);
-            const float dd[4] = {d.x, d.y, d.z, d.w}, xx[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(dd[i], xx[k], acc[i][k]);
-        }
-        __syncthreads();
-    }
-    float* out = part + (((size_t)chunk * 9 + tap) * CH) * CH;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) out[(co4 + i) * CH + ci4 + k] = acc[i][k];
 }
 
 // Sums weight-gradient partials over chunks into the flat gradient layout.
@@ -2832,7 +2796,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         }
         {
             MSF_PROF("wgrad_tc", st);
-            wgrad_tc_kernel<<<wg_ctas, THREADS, WG_SMEM, st>>>(m18[l], g16[cur ^ 1], w.wpart, tg, c->d_err);
+            wgrad_tc_kernel<9><<<wg_ctas, THREADS, WG_SMEM, st>>>(m18[l], g16[cur ^ 1], w.wpart, tg, c->d_err);
             MSF_LAUNCH_CHECK();
         }
         {
@@ -2853,11 +2817,18 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     MSF_TRY(trace_record(c, TRACE_DZ, 0, w.g[cur ^ 1], P, st));
     MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, w.sums));
     {
-        MSF_PROF("train_wgrad", st);
+        MSF_PROF("train_copy_grads", st);
         copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(w.sums, c->d_grad + o.b[0], CH);
-        wgrad_kernel<1><<<dim3(1, nchunks), 256, 0, st>>>((const uint4*)w.g[cur ^ 1], (const uint4*)w.act[0], w.wpart,
-                                                           B, H, W);
-        wgrad_reduce_kernel<<<16, 256, 0, st>>>(w.wpart, nchunks, 1, 1, c->d_grad + o.w[0]);
+        MSF_LAUNCH_CHECK();
+    }
+    {
+        MSF_PROF("wgrad_tc", st);
+        wgrad_tc_kernel<1><<<wg_ctas, THREADS, WG_SMEM, st>>>(m16[0], g16[cur ^ 1], w.wpart, tg, c->d_err);
+        MSF_LAUNCH_CHECK();
+    }
+    {
+        MSF_PROF("wgrad_reduce", st);
+        wgrad_reduce_kernel<<<16, 256, 0, st>>>(w.wpart, wg_ctas, 1, 1, c->d_grad + o.w[0]);
         MSF_LAUNCH_CHECK();
     }
     // ---------------- Adam on everything except the running statistics
