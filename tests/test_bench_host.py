@@ -59,3 +59,39 @@ def test_in_grid_crossings_brute_force():
         # allow a crossing exactly on a boundary to fall either way
         assert abs(got - brute) <= max(2, brute // 1000), (mode, got, brute)
         assert 0 < got < sc.nt * sc.views * sc.nu * sc.nv * n
+
+
+def test_training_lr_schedule():
+    # constant for the first two thirds, then a cosine decay to a tenth
+    steps = 4800
+    lrs = [bench.train_lr(i, steps) for i in range(steps)]
+    assert lrs[0] == lrs[2 * steps // 3] == bench.TRAIN_LR
+    assert all(a >= b for a, b in zip(lrs, lrs[1:]))
+    assert abs(bench.train_lr(steps, steps) - 0.1 * bench.TRAIN_LR) < 1e-12
+    assert min(lrs) > 0.1 * bench.TRAIN_LR - 1e-12
+
+
+def test_quality_points_follow_the_iteration_count():
+    # the trajectory stops at twice the quality iteration count
+    calls = []
+
+    class Fake:
+        def __call__(self, want_residual=False):
+            calls.append(want_residual)
+            return 0.5 if want_residual else None
+
+    import torch
+    x = torch.zeros(4)
+    ref = torch.ones(4)
+    import paper_2008_01567_gb300.metrics as metrics
+    orig = (metrics.psnr, metrics.ssim)
+    metrics.psnr = lambda a, b: 0.0
+    metrics.ssim = lambda a, b: 0.0
+    try:
+        at, traj = bench.quality_run(Fake(), x, ref, 30)
+        assert [t["iter"] for t in traj] == [10, 20, 30, 60] and at["iters"] == 30 and len(calls) == 60
+        calls.clear()
+        at, traj = bench.quality_run(Fake(), x, ref, 2)
+        assert [t["iter"] for t in traj] == [2] and len(calls) == 2
+    finally:
+        metrics.psnr, metrics.ssim = orig
