@@ -2243,14 +2243,15 @@ __global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restr
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // two threads per output: blocks of even and of odd index, then their sum
-    const int o = threadIdx.x & 127, h = threadIdx.x >> 7;
-    double s = 0.0;
-    for (unsigned b = h; b < gridDim.x; b += 2) s += __ldcg(part + ((size_t)b * 2 + (o >> 6)) * CH + (o & 63));
-    double* half = &sh[0][0][0];
-    half[h * 128 + o] = s;
-    __syncthreads();
-    if (threadIdx.x < 128) out[o] = half[o] + half[128 + o];
+    // one warp per output at a time: lane l sums blocks l, l + 32, ... in order,
+    // then a shuffle tree; every output's order of additions is fixed
+    const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    for (int o = wp; o < 2 * CH; o += 8) {
+        double s = 0.0;
+        for (unsigned b = ln; b < gridDim.x; b += 32) s += __ldcg(part + ((size_t)b * 2 + (o >> 6)) * CH + (o & 63));
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (ln == 0) out[o] = s;
+    }
     if (threadIdx.x == 0) *counter = 0u;
 }
 
