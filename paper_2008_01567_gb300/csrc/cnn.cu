@@ -2052,7 +2052,6 @@ struct TrainWS {
     float* bf;                      // [10][64] forward biases
     float* zeros;                   // [64]
     double* loss;                   // [1]
-    unsigned* counter;              // finished blocks of the running channel reduction (0 between launches)
     int nchunks, nred;
 };
 
@@ -2074,7 +2073,7 @@ static size_t train_layout(int64_t P, TrainWS* w, uint8_t* base) {
     t.R = (float*)take((size_t)P * 4);
     t.dR = (float*)take((size_t)P * 4);
     t.nchunks = (int)((P + WG_CHUNK - 1) / WG_CHUNK);
-    t.nred = 4 * 152;
+    t.nred = 2 * 152;
     t.part = (double*)take((size_t)t.nred * 2 * CH * 8);
     t.sums = (double*)take((size_t)8 * 4 * CH * 8);
     t.bnp = (float*)take((size_t)8 * 2 * CH * 4);
@@ -2086,7 +2085,6 @@ static size_t train_layout(int64_t P, TrainWS* w, uint8_t* base) {
     t.bf = (float*)take(LAYERS * CH * 4);
     t.zeros = (float*)take(CH * 4);
     t.loss = (double*)take(8);
-    t.counter = (unsigned*)take(sizeof(unsigned));
     if (w) *w = t;
     return o;
 }
@@ -2163,14 +2161,11 @@ __device__ __forceinline__ void f32x8_load(const float* p, float* f) {
     f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
 }
 
-// The block that finishes last (counted on `counter`, which it resets) sums
-// all blocks' partials in block order into out[2][64].
 template <int MODE>
 __global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restrict__ t0v, const float* __restrict__ t1,
                                                              const float* __restrict__ bnp, const float* __restrict__ gamma,
                                                              const float* __restrict__ beta, size_t P,
-                                                             double* __restrict__ part, unsigned* __restrict__ counter,
-                                                             double* __restrict__ out) {
+                                                             double* __restrict__ part) {
     __shared__ double sh[2][32][65];
     const int lane8 = threadIdx.x & 7, row = threadIdx.x >> 3;
     double s0[8], s1[8];
@@ -2236,23 +2231,14 @@ __global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restr
         for (int r = 0; r < 32; ++r) s += sh[k][r][c];
         part[((size_t)blockIdx.x * 2 + k) * CH + c] = s;
     }
-    __threadfence();
-    __syncthreads();
-    __shared__ bool last;
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // one warp per output at a time: lane l sums blocks l, l + 32, ... in order,
-    // then a shuffle tree; every output's order of additions is fixed
-    const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    for (int o = wp; o < 2 * CH; o += 8) {
-        double s = 0.0;
-        for (unsigned b = ln; b < gridDim.x; b += 32) s += __ldcg(part + ((size_t)b * 2 + (o >> 6)) * CH + (o & 63));
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (ln == 0) out[o] = s;
-    }
-    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Sums the partials of channel_reduce_kernel in block order: out[2][64].
+__global__ void channel_finalize_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+    const int k = threadIdx.x >> 6, c = threadIdx.x & 63;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[((size_t)b * 2 + k) * CH + c];
+    out[k * CH + c] = s;
 }
 
 
@@ -2552,12 +2538,6 @@ extern "C" msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels
     }
     c->train_ws_bytes = bytes;
     c->train_cap = max_train_pixels;
-    {
-        TrainWS w;
-        train_layout(max_train_pixels, &w, (uint8_t*)c->train_ws);
-        if (cudaMemset(w.counter, 0, sizeof(unsigned)) != cudaSuccess)
-            return fail(MSF_ERR_CUDA, "msf_cnn_train_reserve: cannot clear the workspace");
-    }
     return trace_alloc(c);
 }
 
@@ -2714,13 +2694,18 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     const int nred = w.nred;
     auto reduce = [&](int mode, const void* t0, const float* t1, const float* bnp, const float* ga,
                       const float* be, double* out) -> msf_status {
-        MSF_PROF("train_reduce", st);
-        if (mode == RED_MOMENTS)
-            channel_reduce_kernel<RED_MOMENTS><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part, w.counter, out);
-        else if (mode == RED_BNBWD)
-            channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part, w.counter, out);
-        else
-            channel_reduce_kernel<RED_SUM><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part, w.counter, out);
+        {
+            MSF_PROF("train_reduce", st);
+            if (mode == RED_MOMENTS)
+                channel_reduce_kernel<RED_MOMENTS><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+            else if (mode == RED_BNBWD)
+                channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+            else
+                channel_reduce_kernel<RED_SUM><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+            MSF_LAUNCH_CHECK();
+        }
+        MSF_PROF("train_reduce_finalize", st);
+        channel_finalize_kernel<<<1, 128, 0, st>>>(w.part, nred, out);
         MSF_LAUNCH_CHECK();
         return MSF_OK;
     };
