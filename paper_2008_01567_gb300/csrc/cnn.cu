@@ -2233,12 +2233,18 @@ __global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restr
     }
 }
 
-// Sums the partials of channel_reduce_kernel in block order: out[2][64].
-__global__ void channel_finalize_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
-    const int k = threadIdx.x >> 6, c = threadIdx.x & 63;
+// Sums the partials of channel_reduce_kernel into out[2][64], one warp per
+// output: lane l adds blocks l, l+32, ... in order, then a fixed shuffle tree
+// (the same order on every run). Launched as 16 blocks of 256 threads.
+__global__ void __launch_bounds__(256) channel_finalize_kernel(const double* __restrict__ part, int nblk,
+                                                               double* __restrict__ out) {
+    const int o = blockIdx.x * 8 + (threadIdx.x >> 5), ln = threadIdx.x & 31;
+    if (o >= 2 * CH) return;
+    const int k = o >> 6, c = o & 63;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[((size_t)b * 2 + k) * CH + c];
-    out[k * CH + c] = s;
+    for (int b = ln; b < nblk; b += 32) s += part[((size_t)b * 2 + k) * CH + c];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (ln == 0) out[o] = s;
 }
 
 
@@ -2705,7 +2711,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
             MSF_LAUNCH_CHECK();
         }
         MSF_PROF("train_reduce_finalize", st);
-        channel_finalize_kernel<<<1, 128, 0, st>>>(w.part, nred, out);
+        channel_finalize_kernel<<<2 * CH / 8, 256, 0, st>>>(w.part, nred, out);
         MSF_LAUNCH_CHECK();
         return MSF_OK;
     };
