@@ -360,7 +360,8 @@ msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const float* d_clean
 /* Reserves the training workspace for batches of up to max_train_pixels =
  * B*H*W pixels (about 3.7 KB per pixel: every layer's BF16 activations, FP32
  * pre-BatchNorm outputs, gradients and reduction buffers).  Must precede
- * msf_train_step; a larger reservation replaces a smaller one. */
+ * msf_train_step; a larger reservation replaces a smaller one.
+ * MSF_ERR_ARG unless 128 <= max_train_pixels <= 2^28. */
 msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels);
 
 /* Copies the gradients of the last msf_train_step (flat layout of

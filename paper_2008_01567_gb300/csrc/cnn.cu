@@ -2165,15 +2165,15 @@ __device__ __forceinline__ void f32x8_load(const float* p, float* f) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restrict__ t0v, const float* __restrict__ t1,
-                                                             const float* __restrict__ bnp, const float* __restrict__ gamma,
-                                                             const float* __restrict__ beta, size_t P,
-                                                             double* __restrict__ part) {
+__global__ void __launch_bounds__(256, 2) channel_reduce_kernel(const void* __restrict__ t0v, const float* __restrict__ t1,
+                                                                const float* __restrict__ bnp, const float* __restrict__ gamma,
+                                                                const float* __restrict__ beta, size_t P,
+                                                                double* __restrict__ part) {
+    // sh[k][row][c]: this thread's FP64 sums (its 8 channels of pixel row `row`)
     __shared__ double sh[2][32][65];
     const int lane8 = threadIdx.x & 7, row = threadIdx.x >> 3;
-    double s0[8], s1[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s0[i] = s1[i] = 0.0;
+    for (int i = 0; i < 8; ++i) sh[0][row][lane8 * 8 + i] = sh[1][row][lane8 * 8 + i] = 0.0;
     float mean[8], istd[8], ga[8], be[8];
     if (MODE == RED_BNBWD) {
 #pragma unroll
@@ -2186,46 +2186,76 @@ __global__ void __launch_bounds__(256) channel_reduce_kernel(const void* __restr
     }
     // Each thread sums runs of RED_RUN of its pixels in FP32 and adds each run
     // into its FP64 sums (FP64 arithmetic is a small fraction of the FP32 rate
-    // on this GPU); the order of every addition is fixed.
-    constexpr int RED_RUN = 8;
+    // on this GPU); the order of every addition is fixed.  The loads of a run
+    // are issued BATCH at a time before any of them is added (pixels past P
+    // read as zeros, which leave the sums unchanged), so that each thread keeps
+    // several loads in flight.
+    constexpr int RED_RUN = 32;
+    constexpr int BATCH = MODE == RED_BNBWD ? 4 : 8;
     const size_t stride = (size_t)gridDim.x * 32;
-    size_t p = blockIdx.x * (size_t)32 + row;
-    while (p < P) {
+    for (size_t p = blockIdx.x * (size_t)32 + row; p < P; p += RED_RUN * stride) {
         float r0[8], r1[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) r0[i] = r1[i] = 0.0f;
-        for (int k = 0; k < RED_RUN && p < P; ++k, p += stride) {
-            float a[8];
-            if (MODE == RED_MOMENTS) f32x8_load(static_cast<const float*>(t0v) + p * CH + lane8 * 8, a);
-            else bf16x8_to_f32(static_cast<const uint4*>(t0v)[p * 8 + lane8], a);
-            if (MODE == RED_MOMENTS) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) { r0[i] += a[i]; r1[i] = fmaf(a[i], a[i], r1[i]); }
-            } else if (MODE == RED_SUM) {
+        for (int k0 = 0; k0 < RED_RUN; k0 += BATCH) {
+            if (p + (size_t)k0 * stride >= P) break;
+            constexpr bool F32 = MODE == RED_MOMENTS;
+            float4 av[F32 ? BATCH : 1][2];                  // FP32 input
+            uint4 hv[F32 ? 1 : BATCH];                      // BF16 input, converted when added
+            float4 zv[MODE == RED_BNBWD ? BATCH : 1][2];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) r0[i] += a[i];
-            } else {
-                float z[8];
-                f32x8_load(t1 + p * CH + lane8 * 8, z);
+            for (int b = 0; b < BATCH; ++b) {
+                const size_t q = p + (size_t)(k0 + b) * stride;
+                const bool in = q < P;
+                if (F32) {
+                    const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(t0v) + q * CH + lane8 * 8);
+                    av[b][0] = in ? src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    av[b][1] = in ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    hv[b] = in ? static_cast<const uint4*>(t0v)[q * 8 + lane8] : make_uint4(0u, 0u, 0u, 0u);
+                }
+                if (MODE == RED_BNBWD) {
+                    const float4* src = reinterpret_cast<const float4*>(t1 + q * CH + lane8 * 8);
+                    zv[b][0] = in ? src[0] : make_float4(mean[0], mean[1], mean[2], mean[3]);
+                    zv[b][1] = in ? src[1] : make_float4(mean[4], mean[5], mean[6], mean[7]);
+                }
+            }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float xh = (z[i] - mean[i]) * istd[i];
-                    const float dy = (ga[i] * xh + be[i] > 0.0f) ? a[i] : 0.0f;
-                    r0[i] += dy;
-                    r1[i] = fmaf(dy, xh, r1[i]);
+            for (int b = 0; b < BATCH; ++b) {
+                float a[8], z[MODE == RED_BNBWD ? 8 : 1];
+                if (F32) {
+                    a[0] = av[b][0].x; a[1] = av[b][0].y; a[2] = av[b][0].z; a[3] = av[b][0].w;
+                    a[4] = av[b][1].x; a[5] = av[b][1].y; a[6] = av[b][1].z; a[7] = av[b][1].w;
+                } else {
+                    bf16x8_to_f32(hv[b], a);
+                }
+                if (MODE == RED_BNBWD) {
+                    z[0] = zv[b][0].x; z[1] = zv[b][0].y; z[2] = zv[b][0].z; z[3] = zv[b][0].w;
+                    z[4] = zv[b][1].x; z[5] = zv[b][1].y; z[6] = zv[b][1].z; z[7] = zv[b][1].w;
+                }
+                if (MODE == RED_MOMENTS) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) { r0[i] += a[i]; r1[i] = fmaf(a[i], a[i], r1[i]); }
+                } else if (MODE == RED_SUM) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) r0[i] += a[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float xh = (z[i] - mean[i]) * istd[i];
+                        const float dy = (ga[i] * xh + be[i] > 0.0f) ? a[i] : 0.0f;
+                        r0[i] += dy;
+                        r1[i] = fmaf(dy, xh, r1[i]);
+                    }
                 }
             }
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            s0[i] += (double)r0[i];
-            s1[i] += (double)r1[i];
+            sh[0][row][lane8 * 8 + i] += (double)r0[i];
+            sh[1][row][lane8 * 8 + i] += (double)r1[i];
         }
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        sh[0][row][lane8 * 8 + i] = s0[i];
-        sh[1][row][lane8 * 8 + i] = s1[i];
     }
     __syncthreads();
     if (threadIdx.x < 2 * CH) {
@@ -2533,9 +2563,11 @@ __global__ void training_batch_kernel(const float* __restrict__ vol, int nx, int
 
 static msf_status trace_alloc(msf_cnn* c);
 
+
 extern "C" msf_status msf_cnn_train_reserve(msf_cnn* c, int64_t max_train_pixels) {
     MSF_REQUIRE(c, "msf_cnn_train_reserve: NULL handle");
-    MSF_REQUIRE(max_train_pixels >= 128, "msf_cnn_train_reserve: need at least 128 pixels");
+    MSF_REQUIRE(max_train_pixels >= 128 && max_train_pixels <= ((int64_t)1 << 28),
+                "msf_cnn_train_reserve: need 128 to 2^28 pixels, got %lld", (long long)max_train_pixels);
     if (max_train_pixels <= c->train_cap) return MSF_OK;
     cudaFree(c->train_ws);
     c->train_ws = nullptr;

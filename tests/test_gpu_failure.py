@@ -59,7 +59,7 @@ def test_nonfinite_input_is_reported(M):
 
 
 def test_out_of_memory_is_reported_and_recoverable(M):
-    # allocations far beyond the device (2 x 128 TB of activations, ~4 PB of
+    # allocations far beyond the device (2 x 128 TB of activations, ~1 TB of
     # training workspace) fail in cudaMalloc and come back as MSF_ERR_NOMEM;
     # the partial allocations are released and the context keeps working
     import torch
@@ -68,8 +68,11 @@ def test_out_of_memory_is_reported_and_recoverable(M):
     assert e.value.status == 3                 # MSF_ERR_NOMEM
     c = M.Cnn(4096)
     with pytest.raises(M.MsfError) as e:
-        c.train_reserve(1 << 40)
+        c.train_reserve(1 << 28)               # ~1 TB of training workspace
     assert e.value.status == 3
+    with pytest.raises(M.MsfError) as e:
+        c.train_reserve(1 << 40)               # past the 2^28-pixel limit
+    assert e.value.status == 1                 # MSF_ERR_ARG
     c.train_reserve(1 << 12)
     convs, bns = synth.cnn_weights(3)
     c.set_params(M.pack_params(convs, bns))
