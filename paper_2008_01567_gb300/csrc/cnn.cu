@@ -2038,6 +2038,11 @@ namespace cnn {
 
 constexpr float BN_MOMENTUM = 0.1f;
 constexpr int WG_CHUNK = 4096;      // pixels per weight-gradient block
+// Blocks of the elementwise training launches.  Their grid-stride loops step
+// by EW_BLOCKS * 256 elements of 8 channels, a multiple of 8, so a thread keeps
+// the same channel octet (i & 7) for all its elements.
+constexpr int EW_BLOCKS = 152 * 8;
+
 
 // Workspace carved from one allocation.
 struct TrainWS {
@@ -2077,7 +2082,7 @@ static size_t train_layout(int64_t P, TrainWS* w, uint8_t* base) {
     t.dR = (float*)take((size_t)P * 4);
     t.nchunks = (int)((P + WG_CHUNK - 1) / WG_CHUNK);
     t.nred = 2 * 152;
-    t.part = (double*)take((size_t)t.nred * 2 * CH * 8);
+    t.part = (double*)take((size_t)(t.nred > EW_BLOCKS ? t.nred : EW_BLOCKS) * 2 * CH * 8);
     t.sums = (double*)take((size_t)8 * 4 * CH * 8);
     t.bnp = (float*)take((size_t)8 * 2 * CH * 4);
     t.wpart = (float*)take((size_t)(t.nchunks > WG_MAX_CTAS ? t.nchunks : WG_MAX_CTAS) * 9 * CH * CH * 4);
@@ -2151,14 +2156,13 @@ __device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-enum RedMode { RED_MOMENTS = 0, RED_BNBWD = 1, RED_SUM = 2 };
+enum RedMode { RED_MOMENTS = 0, RED_BNBWD = 1 };
 
-// Per-channel sums over P pixels of [P][64] BF16 tensors; 256 threads = 8
+// Per-channel sums over P pixels of [P][64] tensors; 256 threads = 8
 // lanes of 8 channels x 32 pixel rows.  Writes FP64 partials [block][2][64].
 //   RED_MOMENTS: sum z, sum z^2                     (z = t0, FP32)
 //   RED_BNBWD:   sum dy, sum dy*xhat with dy = g * [gamma xhat + beta > 0],
 //                xhat = (z - mean) istd               (g = t0 BF16, z = t1 FP32)
-//   RED_SUM:     sum t0                               (BF16)
 __device__ __forceinline__ void f32x8_load(const float* p, float* f) {
     const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
     f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
@@ -2237,9 +2241,6 @@ __global__ void __launch_bounds__(256, 2) channel_reduce_kernel(const void* __re
                 if (MODE == RED_MOMENTS) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) { r0[i] += a[i]; r1[i] = fmaf(a[i], a[i], r1[i]); }
-                } else if (MODE == RED_SUM) {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) r0[i] += a[i];
                 } else {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -2270,9 +2271,9 @@ __global__ void __launch_bounds__(256, 2) channel_reduce_kernel(const void* __re
 // output: lane l adds blocks l, l+32, ... in order, then a fixed shuffle tree
 // (the same order on every run). Launched as 16 blocks of 256 threads.
 __global__ void __launch_bounds__(256) channel_finalize_kernel(const double* __restrict__ part, int nblk,
-                                                               double* __restrict__ out) {
+                                                               double* __restrict__ out, int nout) {
     const int o = blockIdx.x * 8 + (threadIdx.x >> 5), ln = threadIdx.x & 31;
-    if (o >= 2 * CH) return;
+    if (o >= nout) return;
     const int k = o >> 6, c = o & 63;
     double s = 0.0;
     for (int b = ln; b < nblk; b += 32) s += part[((size_t)b * 2 + k) * CH + c];
@@ -2308,14 +2309,60 @@ __global__ void bn_apply_relu_kernel(const float* __restrict__ z, uint4* __restr
     }
 }
 
+// Per-channel sums of the BF16 values a thread stores (its channel octet):
+// runs of up to 32 elements in FP32, each run added into the thread's FP64
+// sums (kept in shared memory, sh[thread / 8][octet * 8 + k]); then the
+// block's 32 threads of each octet are summed in thread order into
+// part[block][0][64] (part[block][1][*] = 0), the layout channel_finalize_kernel
+// reads.
+struct OctetSums {
+    double (*sh)[CH + 1];
+    float run[8];
+    int n;
+    __device__ __forceinline__ void init(double (*shared)[CH + 1]) {
+        sh = shared;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) run[k] = 0.0f, sh[threadIdx.x >> 3][(threadIdx.x & 7) * 8 + k] = 0.0;
+        n = 0;
+    }
+    __device__ __forceinline__ void add(uint4 v) {
+        float f[8];
+        bf16x8_to_f32(v, f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) run[k] += f[k];
+        if (++n == 32) flush();
+    }
+    __device__ __forceinline__ void flush() {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            sh[threadIdx.x >> 3][(threadIdx.x & 7) * 8 + k] += (double)run[k];
+            run[k] = 0.0f;
+        }
+        n = 0;
+    }
+    __device__ __forceinline__ void store(double* __restrict__ part) {
+        flush();
+        __syncthreads();
+        if (threadIdx.x < CH) {
+            double t = 0.0;
+            for (int r = 0; r < 32; ++r) t += sh[r][threadIdx.x];
+            part[(size_t)blockIdx.x * 2 * CH + threadIdx.x] = t;
+            part[(size_t)blockIdx.x * 2 * CH + CH + threadIdx.x] = 0.0;
+        }
+    }
+};
+
 // dz = gamma istd (dy - sum(dy)/P - xhat sum(dy xhat)/P), dy = g [y > 0].
 // The per-channel factors are formed once per block (the two FP64 means
 // rounded to FP32, as the element loop used them); the element loop is FP32.
+// Also writes the per-block sums of the stored dz (the conv bias gradient) to
+// part (OctetSums; launched with EW_BLOCKS blocks of 256 threads).
 __global__ void __launch_bounds__(256) bn_bwd_apply_kernel(const uint4* __restrict__ g, const float* __restrict__ z,
                                                            uint4* __restrict__ dz, const float* __restrict__ bnp,
                                                            const float* __restrict__ gamma,
                                                            const float* __restrict__ beta,
-                                                           const double* __restrict__ sums, double P, size_t n8) {
+                                                           const double* __restrict__ sums, double P, size_t n8,
+                                                           double* __restrict__ part) {
     __shared__ float s_mean[CH], s_istd[CH], s_g[CH], s_b[CH], s_m1[CH], s_m2[CH];
     if (threadIdx.x < CH) {
         const int c = threadIdx.x;
@@ -2326,6 +2373,9 @@ __global__ void __launch_bounds__(256) bn_bwd_apply_kernel(const uint4* __restri
         s_m1[c] = (float)(sums[c] / P);
         s_m2[c] = (float)(sums[CH + c] / P);
     }
+    __shared__ double bsum[32][CH + 1];
+    OctetSums bias;
+    bias.init(bsum);
     __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
         const int c0 = (int)(i & 7) * 8;
@@ -2339,20 +2389,31 @@ __global__ void __launch_bounds__(256) bn_bwd_apply_kernel(const uint4* __restri
             const float dy = (s_g[c] * xh + s_b[c] > 0.0f) ? gv[k] : 0.0f;
             o[k] = s_g[c] * s_istd[c] * (dy - s_m1[c] - xh * s_m2[c]);
         }
-        dz[i] = f32_to_bf16x8(o);
+        const uint4 v = f32_to_bf16x8(o);
+        dz[i] = v;
+        bias.add(v);
     }
+    bias.store(part);
 }
 
-// dz = g * [a > 0] (layer 1: ReLU without BatchNorm)
-__global__ void relu_bwd_kernel(const uint4* __restrict__ g, const uint4* __restrict__ a, uint4* __restrict__ dz, size_t n8) {
+// dz = g * [a > 0] (layer 1: ReLU without BatchNorm); per-block sums of dz
+// (the conv bias gradient) to part as in bn_bwd_apply_kernel.
+__global__ void __launch_bounds__(256) relu_bwd_kernel(const uint4* __restrict__ g, const uint4* __restrict__ a,
+                                                       uint4* __restrict__ dz, size_t n8, double* __restrict__ part) {
+    __shared__ double bsum[32][CH + 1];
+    OctetSums bias;
+    bias.init(bsum);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
         float gv[8], av[8];
         bf16x8_to_f32(g[i], gv);
         bf16x8_to_f32(a[i], av);
 #pragma unroll
         for (int k = 0; k < 8; ++k) gv[k] = av[k] > 0.0f ? gv[k] : 0.0f;
-        dz[i] = f32_to_bf16x8(gv);
+        const uint4 v = f32_to_bf16x8(gv);
+        dz[i] = v;
+        bias.add(v);
     }
+    bias.store(part);
 }
 
 // out = centre - R; loss partials of (out - clean)^2; dR = -2 (out - clean)/P.
@@ -2739,14 +2800,12 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
             MSF_PROF("train_reduce", st);
             if (mode == RED_MOMENTS)
                 channel_reduce_kernel<RED_MOMENTS><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
-            else if (mode == RED_BNBWD)
-                channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
             else
-                channel_reduce_kernel<RED_SUM><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+                channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
             MSF_LAUNCH_CHECK();
         }
         MSF_PROF("train_reduce_finalize", st);
-        channel_finalize_kernel<<<2 * CH / 8, 256, 0, st>>>(w.part, nred, out);
+        channel_finalize_kernel<<<2 * CH / 8, 256, 0, st>>>(w.part, nred, out, 2 * CH);
         MSF_LAUNCH_CHECK();
         return MSF_OK;
     };
@@ -2809,13 +2868,17 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         }
         {
             MSF_PROF("train_bn_bwd", st);
-            bn_bwd_apply_kernel<<<152 * 8, 256, 0, st>>>((const uint4*)w.g[cur], w.z[l],
-                                                         (uint4*)w.g[cur ^ 1], bnp, ga, be, sums + 2 * CH, (double)P, n8);
+            bn_bwd_apply_kernel<<<EW_BLOCKS, 256, 0, st>>>((const uint4*)w.g[cur], w.z[l], (uint4*)w.g[cur ^ 1], bnp,
+                                                           ga, be, sums + 2 * CH, (double)P, n8, w.part);
             MSF_LAUNCH_CHECK();
         }
         MSF_TRY(trace_record(c, TRACE_DZ, l, w.g[cur ^ 1], P, st));
-        // dz in g[cur ^ 1]: conv bias grad, weight grad, input grad
-        MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, sums));
+        // dz in g[cur ^ 1]: conv bias grad (its block sums came with dz), weight grad, input grad
+        {
+            MSF_PROF("train_reduce_finalize", st);
+            channel_finalize_kernel<<<CH / 8, 256, 0, st>>>(w.part, EW_BLOCKS, sums, CH);
+            MSF_LAUNCH_CHECK();
+        }
         {
             MSF_PROF("train_copy_grads", st);
             copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums, c->d_grad + o.b[l], CH);
@@ -2838,11 +2901,16 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     }
     {
         MSF_PROF("train_first_bwd", st);
-        relu_bwd_kernel<<<152 * 8, 256, 0, st>>>((const uint4*)w.g[cur], (const uint4*)w.act[1], (uint4*)w.g[cur ^ 1], n8);
+        relu_bwd_kernel<<<EW_BLOCKS, 256, 0, st>>>((const uint4*)w.g[cur], (const uint4*)w.act[1], (uint4*)w.g[cur ^ 1],
+                                                   n8, w.part);
         MSF_LAUNCH_CHECK();
     }
     MSF_TRY(trace_record(c, TRACE_DZ, 0, w.g[cur ^ 1], P, st));
-    MSF_TRY(reduce(RED_SUM, w.g[cur ^ 1], nullptr, nullptr, nullptr, nullptr, w.sums));
+    {
+        MSF_PROF("train_reduce_finalize", st);
+        channel_finalize_kernel<<<CH / 8, 256, 0, st>>>(w.part, EW_BLOCKS, w.sums, CH);
+        MSF_LAUNCH_CHECK();
+    }
     {
         MSF_PROF("train_copy_grads", st);
         copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(w.sums, c->d_grad + o.b[0], CH);
