@@ -53,7 +53,10 @@ constexpr int TMEM_COLS = 128;
 // EPI_PART:  last 64 -> 64 layer fused with the output layer (row-pair kernel):
 //            per-tap output-layer sums -> FP32 planes [9][img][H][W]
 // EPI_RAW32: acc + bias -> FP32 [img][H][W][64] (training: pre-BatchNorm outputs,
-//            kept in FP32 because normalising subtracts their batch mean)
+//            kept in FP32 because normalising subtracts their batch mean),
+//            stored by TMA through map_out (make_f32_out_map); the kernel also
+//            writes per-warp partial sums of the outputs and their squares
+//            (the BatchNorm moments) to moments[CTA * 4 + warp][2][64]
 enum Epi { EPI_RELU = 0, EPI_RESID = 1, EPI_RAW = 2, EPI_F32 = 3, EPI_RAW32 = 4, EPI_PART = 5 };
 
 __host__ __device__ constexpr bool epi_stores_bf16(int e) { return e == EPI_RELU || e == EPI_RAW; }
@@ -215,8 +218,11 @@ struct ConvCfg {
     static constexpr int SLOT_BYTES = GROUP * BOX_BYTES;
     static constexpr int W_BYTES = TAPS * N * 128;
     static constexpr int O_BYTES = epi_stores_bf16(EPI) ? TILE_BYTES : 0;
+    // EPI_RAW32: per epilogue warp, its 32 pixels x 64 FP32 outputs of a tile
+    // (the transpose behind the BatchNorm moments)
+    static constexpr int M_BYTES = EPI == EPI_RAW32 ? 4 * 32 * 256 : 0;
     static constexpr int BAR_BYTES = 512;   // barriers, TMEM slot, abort flag (256 B), bias (256 B)
-    static constexpr int SMEM = 1024 + NS * SLOT_BYTES + W_BYTES + O_BYTES + BAR_BYTES;
+    static constexpr int SMEM = 1024 + NS * SLOT_BYTES + W_BYTES + O_BYTES + M_BYTES + BAR_BYTES;
     static_assert(BOXES % GROUP == 0, "a slot group must divide the boxes of a tile");
     static_assert((2 * NS + 5) * 8 + 8 <= 256, "barrier block overflows into the bias");
     static_assert(SMEM <= 232448, "more dynamic shared memory than a CTA may have");
@@ -231,14 +237,16 @@ template <int TAPS, int N, int NS, int EPI>
 __global__ void __launch_bounds__(THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_w,
                const __grid_constant__ CUtensorMap map_out, const float* __restrict__ bias, TileGeom tg,
-               SliceGeom sg, const float* __restrict__ centre, float* __restrict__ outv, int* __restrict__ err) {
+               SliceGeom sg, const float* __restrict__ centre, float* __restrict__ outv, double* __restrict__ moments,
+               int* __restrict__ err) {
     using C = ConvCfg<TAPS, N, NS, EPI>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sW = sA + NS * C::SLOT_BYTES;
     uint8_t* sO = sW + C::W_BYTES;
-    uint64_t* bars = (uint64_t*)(sO + C::O_BYTES);
+    uint8_t* sM = sO + C::O_BYTES;
+    uint64_t* bars = (uint64_t*)(sM + C::M_BYTES);
     uint64_t* full = bars;
     uint64_t* empty = bars + NS;
     uint64_t* tfull = bars + 2 * NS;
@@ -362,6 +370,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
         // ---------------- epilogue: 4 warps, TMEM lane quarter = warp % 4
         const int q = warp & 3;
         const int row = q * 32 + lane;           // accumulator row = pixel of the tile
+        // EPI_RAW32: this warp's BatchNorm moments of channels 2 lane, 2 lane + 1
+        double msum[2] = {0.0, 0.0}, msq[2] = {0.0, 0.0};
         int it = 0;
         for (int tile = blockIdx.x; tile < tg.total; tile += gridDim.x, ++it) {
             const int ab = it & 1, ua = it >> 1;
@@ -411,16 +421,50 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                     tc::tma_store_commit();
                 }
             } else if (EPI == EPI_RAW32) {
+                static_assert(EPI != EPI_RAW32 || N == CH, "moments are summed for 64 channels");
                 const int a = a0 + row / TILE_B, b = b0 + row % TILE_B;
-                if (a < tg.H && b < tg.W) {
-                    float4* dst = reinterpret_cast<float4*>(outv + (((size_t)img * tg.H + a) * tg.W + b) * N);
+                const bool in = a < tg.H && b < tg.W;
+                float v[N];
 #pragma unroll
-                    for (int j = 0; j < N / 4; ++j)
-                        dst[j] = make_float4(__uint_as_float(r[4 * j]) + sbias[4 * j],
-                                             __uint_as_float(r[4 * j + 1]) + sbias[4 * j + 1],
-                                             __uint_as_float(r[4 * j + 2]) + sbias[4 * j + 2],
-                                             __uint_as_float(r[4 * j + 3]) + sbias[4 * j + 3]);
+                for (int j = 0; j < N; ++j) v[j] = in ? __uint_as_float(r[j]) + sbias[j] : 0.0f;
+                // the warp's 4 x 8 pixels are staged in its own 8 KB as two
+                // boxes of 32 channels (pixel = 128-byte row, 16-byte chunks in
+                // the 128-byte swizzle) and leave by two TMA stores; the staged
+                // copy also gives the BatchNorm moments: lane l sums channels
+                // 2l, 2l + 1 over the 32 pixels in FP32 and adds the tile's sums
+                // into its FP64 moments.  The previous tile's stores must have
+                // read the buffer first.
+                uint8_t* tr = sM + q * (32 * 256);
+                if (lane == 0) tc::tma_store_wait_read<0>();
+                __syncwarp();
+#pragma unroll
+                for (int c = 0; c < N / 4; ++c)
+                    *reinterpret_cast<float4*>(tr + (c >> 3) * 4096 + lane * 128 + (((c & 7) ^ (lane & 7)) << 4)) =
+                        make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    if (a0 + q * (TILE_A / 4) < tg.H) {
+                        tc::tma_store_4d(&map_out, tr, 0, b0, a0 + q * (TILE_A / 4), img);
+                        tc::tma_store_4d(&map_out, tr + 4096, 32, b0, a0 + q * (TILE_A / 4), img);
+                    }
+                    tc::tma_store_commit();
                 }
+                float s0 = 0.0f, s1 = 0.0f, q0 = 0.0f, q1 = 0.0f;
+                const uint8_t* col = tr + (lane >> 4) * 4096 + (lane & 1) * 8;
+                const int chunk = (lane & 15) >> 1;
+#pragma unroll 8
+                for (int rr = 0; rr < 32; ++rr) {
+                    const float2 x = *reinterpret_cast<const float2*>(col + rr * 128 + ((chunk ^ (rr & 7)) << 4));
+                    s0 += x.x;
+                    s1 += x.y;
+                    q0 = fmaf(x.x, x.x, q0);
+                    q1 = fmaf(x.y, x.y, q1);
+                }
+                msum[0] += (double)s0;
+                msum[1] += (double)s1;
+                msq[0] += (double)q0;
+                msq[1] += (double)q1;
             } else {
                 const float R = __uint_as_float(r[0]) + sbias[0];
                 const int a = a0 + row / TILE_B, b = b0 + row % TILE_B;
@@ -435,7 +479,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                 }
             }
         }
-        if (epi_stores_bf16(EPI) && lane == 0) tc::tma_store_wait_all();
+        if ((epi_stores_bf16(EPI) || EPI == EPI_RAW32) && lane == 0) tc::tma_store_wait_all();
+        if (EPI == EPI_RAW32) {
+            // partials [blockIdx.x * 4 + q][2][64]: sum z, sum z^2
+            double* dst = moments + (size_t)(blockIdx.x * 4 + q) * 2 * CH;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                dst[2 * lane + k] = msum[k];
+                dst[CH + 2 * lane + k] = msq[k];
+            }
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1409,6 +1462,23 @@ static msf_status make_act_map(CUtensorMap* m, void* base, int imgs, int H, int 
     return MSF_OK;
 }
 
+// 4D FP32 tensor [imgs][H][W][64] (pre-BatchNorm outputs) for TMA stores of
+// one epilogue warp's 4 x 8 pixels, in two boxes of 32 channels (128 bytes,
+// the widest inner box the 128-byte swizzle takes).
+static msf_status make_f32_out_map(CUtensorMap* m, void* base, int imgs, int H, int W) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[4] = {(cuuint64_t)CH, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)imgs};
+    cuuint64_t strides[3] = {(cuuint64_t)CH * 4, (cuuint64_t)W * CH * 4, (cuuint64_t)H * W * CH * 4};
+    cuuint32_t box[4] = {32, (cuuint32_t)TILE_B, (cuuint32_t)(TILE_A / 4), 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MSF_ERR_CUDA, "cuTensorMapEncodeTiled (FP32 outputs) failed: %d", (int)r);
+    return MSF_OK;
+}
+
 // 2D BF16 weights [rows_total][64] with a box of 64 x rows.
 static msf_status make_w_map(CUtensorMap* m, void* base, int rows_total, int box_rows) {
     EncodeTiledFn enc = encode_fn();
@@ -1519,7 +1589,7 @@ static msf_status ensure_kernel_attrs() {
 template <int TAPS, int N, int NS, int EPI>
 static msf_status launch_conv(const CUtensorMap& ma, const CUtensorMap& mw, const CUtensorMap& mo, const float* bias,
                               const TileGeom& tg, const SliceGeom& sg, const float* centre, float* outv, int* err,
-                              cudaStream_t st) {
+                              cudaStream_t st, double* moments = nullptr) {
     using C = ConvCfg<TAPS, N, NS, EPI>;
     auto kern = conv_tc_kernel<TAPS, N, NS, EPI>;
     MSF_TRY(ensure_kernel_attrs());
@@ -1529,7 +1599,8 @@ static msf_status launch_conv(const CUtensorMap& ma, const CUtensorMap& mw, cons
                        : (N == 16 ? "conv10_tc"
                                   : (EPI == EPI_RAW ? "conv3x3_dgrad_tc" : (EPI == EPI_RAW32 ? "conv3x3_fp32_tc" : "conv3x3_tc"))),
              st);
-    kern<<<grid, THREADS, C::SMEM, st>>>(ma, mw, mo, bias, tg, sg, centre, outv, err);
+    if (EPI == EPI_RAW32 && !moments) return fail(MSF_ERR_ARG, "launch_conv: FP32 outputs need a moments buffer");
+    kern<<<grid, THREADS, C::SMEM, st>>>(ma, mw, mo, bias, tg, sg, centre, outv, moments, err);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
 }
@@ -2156,46 +2227,40 @@ __device__ __forceinline__ uint4 f32_to_bf16x8(const float* f) {
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-enum RedMode { RED_MOMENTS = 0, RED_BNBWD = 1 };
-
-// Per-channel sums over P pixels of [P][64] tensors; 256 threads = 8
-// lanes of 8 channels x 32 pixel rows.  Writes FP64 partials [block][2][64].
-//   RED_MOMENTS: sum z, sum z^2                     (z = t0, FP32)
-//   RED_BNBWD:   sum dy, sum dy*xhat with dy = g * [gamma xhat + beta > 0],
-//                xhat = (z - mean) istd               (g = t0 BF16, z = t1 FP32)
 __device__ __forceinline__ void f32x8_load(const float* p, float* f) {
     const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
     f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256, 2) channel_reduce_kernel(const void* __restrict__ t0v, const float* __restrict__ t1,
-                                                                const float* __restrict__ bnp, const float* __restrict__ gamma,
-                                                                const float* __restrict__ beta, size_t P,
-                                                                double* __restrict__ part) {
+// The two channel sums of the BatchNorm backward over P pixels: sum dy and
+// sum dy*xhat with dy = g * [gamma xhat + beta > 0], xhat = (z - mean) istd
+// (g: BF16 [P][64], z: FP32 [P][64]).  256 threads = 8 lanes of 8 channels x
+// 32 pixel rows; writes FP64 partials [block][2][64].
+__global__ void __launch_bounds__(256, 2) bn_bwd_reduce_kernel(const uint4* __restrict__ g, const float* __restrict__ z,
+                                                               const float* __restrict__ bnp,
+                                                               const float* __restrict__ gamma,
+                                                               const float* __restrict__ beta, size_t P,
+                                                               double* __restrict__ part) {
     // sh[k][row][c]: this thread's FP64 sums (its 8 channels of pixel row `row`)
     __shared__ double sh[2][32][65];
     const int lane8 = threadIdx.x & 7, row = threadIdx.x >> 3;
 #pragma unroll
     for (int i = 0; i < 8; ++i) sh[0][row][lane8 * 8 + i] = sh[1][row][lane8 * 8 + i] = 0.0;
     float mean[8], istd[8], ga[8], be[8];
-    if (MODE == RED_BNBWD) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            mean[i] = bnp[lane8 * 8 + i];
-            istd[i] = bnp[CH + lane8 * 8 + i];
-            ga[i] = gamma[lane8 * 8 + i];
-            be[i] = beta[lane8 * 8 + i];
-        }
+    for (int i = 0; i < 8; ++i) {
+        mean[i] = bnp[lane8 * 8 + i];
+        istd[i] = bnp[CH + lane8 * 8 + i];
+        ga[i] = gamma[lane8 * 8 + i];
+        be[i] = beta[lane8 * 8 + i];
     }
     // Each thread sums runs of RED_RUN of its pixels in FP32 and adds each run
     // into its FP64 sums (FP64 arithmetic is a small fraction of the FP32 rate
     // on this GPU); the order of every addition is fixed.  The loads of a run
     // are issued BATCH at a time before any of them is added (pixels past P
-    // read as zeros, which leave the sums unchanged), so that each thread keeps
-    // several loads in flight.
-    constexpr int RED_RUN = 32;
-    constexpr int BATCH = MODE == RED_BNBWD ? 4 : 8;
+    // read as g = 0, which leaves the sums unchanged), so that each thread
+    // keeps several loads in flight.
+    constexpr int RED_RUN = 32, BATCH = 4;
     const size_t stride = (size_t)gridDim.x * 32;
     for (size_t p = blockIdx.x * (size_t)32 + row; p < P; p += RED_RUN * stride) {
         float r0[8], r1[8];
@@ -2204,51 +2269,29 @@ __global__ void __launch_bounds__(256, 2) channel_reduce_kernel(const void* __re
 #pragma unroll
         for (int k0 = 0; k0 < RED_RUN; k0 += BATCH) {
             if (p + (size_t)k0 * stride >= P) break;
-            constexpr bool F32 = MODE == RED_MOMENTS;
-            float4 av[F32 ? BATCH : 1][2];                  // FP32 input
-            uint4 hv[F32 ? 1 : BATCH];                      // BF16 input, converted when added
-            float4 zv[MODE == RED_BNBWD ? BATCH : 1][2];
+            uint4 hv[BATCH];
+            float4 zv[BATCH][2];
 #pragma unroll
             for (int b = 0; b < BATCH; ++b) {
                 const size_t q = p + (size_t)(k0 + b) * stride;
                 const bool in = q < P;
-                if (F32) {
-                    const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(t0v) + q * CH + lane8 * 8);
-                    av[b][0] = in ? src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    av[b][1] = in ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
-                } else {
-                    hv[b] = in ? static_cast<const uint4*>(t0v)[q * 8 + lane8] : make_uint4(0u, 0u, 0u, 0u);
-                }
-                if (MODE == RED_BNBWD) {
-                    const float4* src = reinterpret_cast<const float4*>(t1 + q * CH + lane8 * 8);
-                    zv[b][0] = in ? src[0] : make_float4(mean[0], mean[1], mean[2], mean[3]);
-                    zv[b][1] = in ? src[1] : make_float4(mean[4], mean[5], mean[6], mean[7]);
-                }
+                hv[b] = in ? g[q * 8 + lane8] : make_uint4(0u, 0u, 0u, 0u);
+                const float4* src = reinterpret_cast<const float4*>(z + q * CH + lane8 * 8);
+                zv[b][0] = in ? src[0] : make_float4(mean[0], mean[1], mean[2], mean[3]);
+                zv[b][1] = in ? src[1] : make_float4(mean[4], mean[5], mean[6], mean[7]);
             }
 #pragma unroll
             for (int b = 0; b < BATCH; ++b) {
-                float a[8], z[MODE == RED_BNBWD ? 8 : 1];
-                if (F32) {
-                    a[0] = av[b][0].x; a[1] = av[b][0].y; a[2] = av[b][0].z; a[3] = av[b][0].w;
-                    a[4] = av[b][1].x; a[5] = av[b][1].y; a[6] = av[b][1].z; a[7] = av[b][1].w;
-                } else {
-                    bf16x8_to_f32(hv[b], a);
-                }
-                if (MODE == RED_BNBWD) {
-                    z[0] = zv[b][0].x; z[1] = zv[b][0].y; z[2] = zv[b][0].z; z[3] = zv[b][0].w;
-                    z[4] = zv[b][1].x; z[5] = zv[b][1].y; z[6] = zv[b][1].z; z[7] = zv[b][1].w;
-                }
-                if (MODE == RED_MOMENTS) {
+                float a[8];
+                bf16x8_to_f32(hv[b], a);
+                const float zz[8] = {zv[b][0].x, zv[b][0].y, zv[b][0].z, zv[b][0].w,
+                                     zv[b][1].x, zv[b][1].y, zv[b][1].z, zv[b][1].w};
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) { r0[i] += a[i]; r1[i] = fmaf(a[i], a[i], r1[i]); }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float xh = (z[i] - mean[i]) * istd[i];
-                        const float dy = (ga[i] * xh + be[i] > 0.0f) ? a[i] : 0.0f;
-                        r0[i] += dy;
-                        r1[i] = fmaf(dy, xh, r1[i]);
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    const float xh = (zz[i] - mean[i]) * istd[i];
+                    const float dy = (ga[i] * xh + be[i] > 0.0f) ? a[i] : 0.0f;
+                    r0[i] += dy;
+                    r1[i] = fmaf(dy, xh, r1[i]);
                 }
             }
         }
@@ -2267,7 +2310,7 @@ __global__ void __launch_bounds__(256, 2) channel_reduce_kernel(const void* __re
     }
 }
 
-// Sums the partials of channel_reduce_kernel into out[2][64], one warp per
+// Sums per-block channel partials [nblk][2][64] into out[nout], one warp per
 // output: lane l adds blocks l, l+32, ... in order, then a fixed shuffle tree
 // (the same order on every run). Launched as 16 blocks of 256 threads.
 __global__ void __launch_bounds__(256) channel_finalize_kernel(const double* __restrict__ part, int nblk,
@@ -2770,7 +2813,8 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         MSF_LAUNCH_CHECK();
         MSF_TRY_CUDA(cudaMemsetAsync(w.zeros, 0, CH * 4, st));
     }
-    CUtensorMap m16[LAYERS], m18[LAYERS], m4[LAYERS], g16[2], g18[2], g4[2], mw[LAYERS], mb[8];
+    CUtensorMap m16[LAYERS], m18[LAYERS], m4[LAYERS], g16[2], g18[2], g4[2], mw[LAYERS], mb[8], f4[LAYERS - 1];
+    for (int l = 1; l < LAYERS - 1; ++l) MSF_TRY(make_f32_out_map(&f4[l], w.z[l], B, H, W));
     for (int l = 0; l < LAYERS; ++l) {
         MSF_TRY(make_act_map(&m16[l], w.act[l], B, H, W, TILE_A));
         MSF_TRY(make_act_map(&m18[l], w.act[l], B, H, W, TILE_A + 2));
@@ -2794,14 +2838,14 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     int wg_ctas = g_num_sms < WG_MAX_CTAS ? g_num_sms : WG_MAX_CTAS;
     if (wg_ctas > tg.total) wg_ctas = tg.total;
     const int nred = w.nred;
-    auto reduce = [&](int mode, const void* t0, const float* t1, const float* bnp, const float* ga,
-                      const float* be, double* out) -> msf_status {
+    // CTAs of the persistent 16 x 8 convs (as launch_conv sizes them)
+    const int conv_grid = tg.total < g_num_sms ? tg.total : g_num_sms;
+    // the BatchNorm backward's two channel sums of layer l into out[2][64]
+    auto bn_bwd_sums = [&](const __nv_bfloat16* g, const float* z, const float* bnp, const float* ga, const float* be,
+                           double* out) -> msf_status {
         {
             MSF_PROF("train_reduce", st);
-            if (mode == RED_MOMENTS)
-                channel_reduce_kernel<RED_MOMENTS><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
-            else
-                channel_reduce_kernel<RED_BNBWD><<<nred, 256, 0, st>>>(t0, t1, bnp, ga, be, P, w.part);
+            bn_bwd_reduce_kernel<<<nred, 256, 0, st>>>((const uint4*)g, z, bnp, ga, be, P, w.part);
             MSF_LAUNCH_CHECK();
         }
         MSF_PROF("train_reduce_finalize", st);
@@ -2818,10 +2862,16 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     }
     MSF_TRY((launch_conv<1, 64, NS_1X1, EPI_RELU>(m16[0], mw[0], m4[1], w.bf, tg, sg, nullptr, nullptr, c->d_err, st)));
     for (int l = 1; l <= 8; ++l) {
-        MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RAW32>(m18[l], mw[l], m4[l], w.bf + l * CH, tg, sg, nullptr, w.z[l], c->d_err, st)));
+        // the conv also sums the BatchNorm moments of its outputs, per epilogue warp
+        MSF_TRY((launch_conv<9, 64, NS_3X3, EPI_RAW32>(m18[l], mw[l], f4[l], w.bf + l * CH, tg, sg, nullptr, w.z[l],
+                                                      c->d_err, st, w.part)));
         double* sums = w.sums + (size_t)(l - 1) * 4 * CH;
         float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
-        MSF_TRY(reduce(RED_MOMENTS, w.z[l], nullptr, nullptr, nullptr, nullptr, sums));
+        {
+            MSF_PROF("train_reduce_finalize", st);
+            channel_finalize_kernel<<<2 * CH / 8, 256, 0, st>>>(w.part, 4 * conv_grid, sums, 2 * CH);
+            MSF_LAUNCH_CHECK();
+        }
         {
             MSF_PROF("train_bn_stats", st);
             bn_stats_kernel<<<1, CH, 0, st>>>(sums, bnp, c->d_params + o.mean[l], c->d_params + o.var[l], (double)P);
@@ -2858,7 +2908,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
         const float* ga = c->d_params + o.gamma[l];
         const float* be = c->d_params + o.beta[l];
-        MSF_TRY(reduce(RED_BNBWD, w.g[cur], w.z[l], bnp, ga, be, sums + 2 * CH));
+        MSF_TRY(bn_bwd_sums(w.g[cur], w.z[l], bnp, ga, be, sums + 2 * CH));
         {
             MSF_PROF("train_copy_grads", st);
             // d gamma = sum dy xhat, d beta = sum dy
