@@ -2310,33 +2310,57 @@ __global__ void __launch_bounds__(256, 2) bn_bwd_reduce_kernel(const uint4* __re
     }
 }
 
-// Sums per-block channel partials [nblk][2][64] into out[nout], one warp per
-// output: lane l adds blocks l, l+32, ... in order, then a fixed shuffle tree
-// (the same order on every run). Launched as 16 blocks of 256 threads.
-__global__ void __launch_bounds__(256) channel_finalize_kernel(const double* __restrict__ part, int nblk,
-                                                               double* __restrict__ out, int nout) {
-    const int o = blockIdx.x * 8 + (threadIdx.x >> 5), ln = threadIdx.x & 31;
-    if (o >= nout) return;
-    const int k = o >> 6, c = o & 63;
+// Sum over the nblk per-block partials [nblk][2][64] of entry (k, c), by one
+// warp: lane l adds blocks l, l+32, ... in order, then a fixed shuffle tree
+// (the same order on every run); the result is in lane 0.
+__device__ __forceinline__ double warp_partial_sum(const double* __restrict__ part, int nblk, int k, int c, int ln) {
     double s = 0.0;
     for (int b = ln; b < nblk; b += 32) s += part[((size_t)b * 2 + k) * CH + c];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (ln == 0) out[o] = s;
+    return s;
+}
+
+// Sums per-block channel partials [nblk][2][64] into out[nout], one warp per
+// output (launched as nout / 8 blocks of 256 threads).  Optionally also as
+// FP32 into lo32[c] (outputs 0..63) and hi32[c] (outputs 64..127), the
+// gradient entries they are.
+__global__ void __launch_bounds__(256) channel_finalize_kernel(const double* __restrict__ part, int nblk,
+                                                               double* __restrict__ out, int nout,
+                                                               float* __restrict__ lo32, float* __restrict__ hi32) {
+    const int o = blockIdx.x * 8 + (threadIdx.x >> 5), ln = threadIdx.x & 31;
+    if (o >= nout) return;
+    const double s = warp_partial_sum(part, nblk, o >> 6, o & 63, ln);
+    if (ln == 0) {
+        out[o] = s;
+        float* d32 = o < CH ? lo32 : hi32;
+        if (d32) d32[o & 63] = (float)s;
+    }
+}
+
+// The BatchNorm moments of one layer from the conv's per-warp partials: sums
+// (sum z, sum z^2) into sums[2][64], then the batch statistics (biased
+// variance) into bnp = (mean, 1/std) and the running statistics (momentum 0.1,
+// unbiased variance).  One warp per channel, 8 blocks of 256 threads.
+__global__ void __launch_bounds__(256) bn_moments_kernel(const double* __restrict__ part, int nblk,
+                                                         double* __restrict__ sums, float* __restrict__ bnp,
+                                                         float* __restrict__ rmean, float* __restrict__ rvar, double P) {
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5), ln = threadIdx.x & 31;
+    if (c >= CH) return;
+    const double s = warp_partial_sum(part, nblk, 0, c, ln);
+    const double s2 = warp_partial_sum(part, nblk, 1, c, ln);
+    if (ln == 0) {
+        sums[c] = s;
+        sums[CH + c] = s2;
+        const double mean = s / P;
+        const double var = fmax(s2 / P - mean * mean, 0.0);
+        bnp[c] = (float)mean;
+        bnp[CH + c] = (float)(1.0 / sqrt(var + (double)BN_EPS));
+        rmean[c] = (1.0f - BN_MOMENTUM) * rmean[c] + BN_MOMENTUM * (float)mean;
+        rvar[c] = (1.0f - BN_MOMENTUM) * rvar[c] + BN_MOMENTUM * (float)(var * P / (P > 1 ? P - 1 : 1));
+    }
 }
 
 
-// Batch statistics (biased variance) and the running-statistics update
-// (momentum 0.1, unbiased variance) of one BatchNorm layer.
-__global__ void bn_stats_kernel(const double* __restrict__ sums, float* __restrict__ bnp, float* __restrict__ rmean,
-                                float* __restrict__ rvar, double P) {
-    const int c = threadIdx.x;
-    const double mean = sums[c] / P;
-    const double var = fmax(sums[CH + c] / P - mean * mean, 0.0);
-    bnp[c] = (float)mean;
-    bnp[CH + c] = (float)(1.0 / sqrt(var + (double)BN_EPS));
-    rmean[c] = (1.0f - BN_MOMENTUM) * rmean[c] + BN_MOMENTUM * (float)mean;
-    rvar[c] = (1.0f - BN_MOMENTUM) * rvar[c] + BN_MOMENTUM * (float)(var * P / (P > 1 ? P - 1 : 1));
-}
 
 // a = relu(gamma (z - mean) istd + beta)
 __global__ void bn_apply_relu_kernel(const float* __restrict__ z, uint4* __restrict__ a, const float* __restrict__ bnp,
@@ -2585,11 +2609,6 @@ __global__ void store_sum_kernel(const double* __restrict__ part, int n, float* 
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
     s = block_sum_f64(s);
     if (threadIdx.x == 0) *out = (float)s;
-}
-
-__global__ void copy_f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
 }
 
 // Adam (Kingma & Ba 2015) with bias correction: c1 = 1/(1-b1^t), c2 = 1/(1-b2^t).
@@ -2842,14 +2861,14 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     const int conv_grid = tg.total < g_num_sms ? tg.total : g_num_sms;
     // the BatchNorm backward's two channel sums of layer l into out[2][64]
     auto bn_bwd_sums = [&](const __nv_bfloat16* g, const float* z, const float* bnp, const float* ga, const float* be,
-                           double* out) -> msf_status {
+                           double* out, float* lo32, float* hi32) -> msf_status {
         {
             MSF_PROF("train_reduce", st);
             bn_bwd_reduce_kernel<<<nred, 256, 0, st>>>((const uint4*)g, z, bnp, ga, be, P, w.part);
             MSF_LAUNCH_CHECK();
         }
         MSF_PROF("train_reduce_finalize", st);
-        channel_finalize_kernel<<<2 * CH / 8, 256, 0, st>>>(w.part, nred, out, 2 * CH);
+        channel_finalize_kernel<<<2 * CH / 8, 256, 0, st>>>(w.part, nred, out, 2 * CH, lo32, hi32);
         MSF_LAUNCH_CHECK();
         return MSF_OK;
     };
@@ -2868,13 +2887,9 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         double* sums = w.sums + (size_t)(l - 1) * 4 * CH;
         float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
         {
-            MSF_PROF("train_reduce_finalize", st);
-            channel_finalize_kernel<<<2 * CH / 8, 256, 0, st>>>(w.part, 4 * conv_grid, sums, 2 * CH);
-            MSF_LAUNCH_CHECK();
-        }
-        {
             MSF_PROF("train_bn_stats", st);
-            bn_stats_kernel<<<1, CH, 0, st>>>(sums, bnp, c->d_params + o.mean[l], c->d_params + o.var[l], (double)P);
+            bn_moments_kernel<<<CH / 8, 256, 0, st>>>(w.part, 4 * conv_grid, sums, bnp, c->d_params + o.mean[l],
+                                                      c->d_params + o.var[l], (double)P);
             MSF_LAUNCH_CHECK();
         }
         {
@@ -2908,14 +2923,8 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         float* bnp = w.bnp + (size_t)(l - 1) * 2 * CH;
         const float* ga = c->d_params + o.gamma[l];
         const float* be = c->d_params + o.beta[l];
-        MSF_TRY(bn_bwd_sums(w.g[cur], w.z[l], bnp, ga, be, sums + 2 * CH));
-        {
-            MSF_PROF("train_copy_grads", st);
-            // d gamma = sum dy xhat, d beta = sum dy
-            copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums + 3 * CH, c->d_grad + o.gamma[l], CH);
-            copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums + 2 * CH, c->d_grad + o.beta[l], CH);
-            MSF_LAUNCH_CHECK();
-        }
+        // d beta = sum dy, d gamma = sum dy xhat
+        MSF_TRY(bn_bwd_sums(w.g[cur], w.z[l], bnp, ga, be, sums + 2 * CH, c->d_grad + o.beta[l], c->d_grad + o.gamma[l]));
         {
             MSF_PROF("train_bn_bwd", st);
             bn_bwd_apply_kernel<<<EW_BLOCKS, 256, 0, st>>>((const uint4*)w.g[cur], w.z[l], (uint4*)w.g[cur ^ 1], bnp,
@@ -2926,12 +2935,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         // dz in g[cur ^ 1]: conv bias grad (its block sums came with dz), weight grad, input grad
         {
             MSF_PROF("train_reduce_finalize", st);
-            channel_finalize_kernel<<<CH / 8, 256, 0, st>>>(w.part, EW_BLOCKS, sums, CH);
-            MSF_LAUNCH_CHECK();
-        }
-        {
-            MSF_PROF("train_copy_grads", st);
-            copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(sums, c->d_grad + o.b[l], CH);
+            channel_finalize_kernel<<<CH / 8, 256, 0, st>>>(w.part, EW_BLOCKS, sums, CH, c->d_grad + o.b[l], nullptr);
             MSF_LAUNCH_CHECK();
         }
         {
@@ -2958,12 +2962,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     MSF_TRY(trace_record(c, TRACE_DZ, 0, w.g[cur ^ 1], P, st));
     {
         MSF_PROF("train_reduce_finalize", st);
-        channel_finalize_kernel<<<CH / 8, 256, 0, st>>>(w.part, EW_BLOCKS, w.sums, CH);
-        MSF_LAUNCH_CHECK();
-    }
-    {
-        MSF_PROF("train_copy_grads", st);
-        copy_f64_to_f32_kernel<<<1, CH, 0, st>>>(w.sums, c->d_grad + o.b[0], CH);
+        channel_finalize_kernel<<<CH / 8, 256, 0, st>>>(w.part, EW_BLOCKS, w.sums, CH, c->d_grad + o.b[0], nullptr);
         MSF_LAUNCH_CHECK();
     }
     {
