@@ -2363,15 +2363,27 @@ __global__ void __launch_bounds__(256) bn_moments_kernel(const double* __restric
 
 
 // a = relu(gamma (z - mean) istd + beta)
-__global__ void bn_apply_relu_kernel(const float* __restrict__ z, uint4* __restrict__ a, const float* __restrict__ bnp,
-                                     const float* __restrict__ gamma, const float* __restrict__ beta, size_t n8) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
-        const int c0 = (int)(i & 7) * 8;
+// (launched with EW_BLOCKS blocks of 256 threads: a thread keeps one channel
+// octet, whose parameters it loads once)
+__global__ void __launch_bounds__(256) bn_apply_relu_kernel(const float* __restrict__ z, uint4* __restrict__ a,
+                                                            const float* __restrict__ bnp,
+                                                            const float* __restrict__ gamma,
+                                                            const float* __restrict__ beta, size_t n8) {
+    const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const int c0 = (int)(i0 & 7) * 8;
+    float ga[8], mu[8], is[8], be[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        ga[k] = gamma[c0 + k];
+        mu[k] = bnp[c0 + k];
+        is[k] = bnp[CH + c0 + k];
+        be[k] = beta[c0 + k];
+    }
+    for (size_t i = i0; i < n8; i += (size_t)gridDim.x * blockDim.x) {
         float v[8];
         f32x8_load(z + i * 8, v);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            v[k] = fmaxf(gamma[c0 + k] * (v[k] - bnp[c0 + k]) * bnp[CH + c0 + k] + beta[c0 + k], 0.0f);
+        for (int k = 0; k < 8; ++k) v[k] = fmaxf(ga[k] * (v[k] - mu[k]) * is[k] + be[k], 0.0f);
         a[i] = f32_to_bf16x8(v);
     }
 }
@@ -2430,7 +2442,7 @@ __global__ void __launch_bounds__(256) bn_bwd_apply_kernel(const uint4* __restri
                                                            const float* __restrict__ beta,
                                                            const double* __restrict__ sums, double P, size_t n8,
                                                            double* __restrict__ part) {
-    __shared__ float s_mean[CH], s_istd[CH], s_g[CH], s_b[CH], s_m1[CH], s_m2[CH];
+    __shared__ __align__(16) float s_mean[CH], s_istd[CH], s_g[CH], s_b[CH], s_m1[CH], s_m2[CH];
     if (threadIdx.x < CH) {
         const int c = threadIdx.x;
         s_mean[c] = bnp[c];
@@ -2446,15 +2458,20 @@ __global__ void __launch_bounds__(256) bn_bwd_apply_kernel(const uint4* __restri
     __syncthreads();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
         const int c0 = (int)(i & 7) * 8;
-        float gv[8], zv[8], o[8];
+        float gv[8], zv[8], o[8], mu[8], is[8], ga[8], be[8], m1[8], m2[8];
         bf16x8_to_f32(g[i], gv);
         f32x8_load(z + i * 8, zv);
+        f32x8_load(s_mean + c0, mu);
+        f32x8_load(s_istd + c0, is);
+        f32x8_load(s_g + c0, ga);
+        f32x8_load(s_b + c0, be);
+        f32x8_load(s_m1 + c0, m1);
+        f32x8_load(s_m2 + c0, m2);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int c = c0 + k;
-            const float xh = (zv[k] - s_mean[c]) * s_istd[c];
-            const float dy = (s_g[c] * xh + s_b[c] > 0.0f) ? gv[k] : 0.0f;
-            o[k] = s_g[c] * s_istd[c] * (dy - s_m1[c] - xh * s_m2[c]);
+            const float xh = (zv[k] - mu[k]) * is[k];
+            const float dy = (ga[k] * xh + be[k] > 0.0f) ? gv[k] : 0.0f;
+            o[k] = ga[k] * is[k] * (dy - m1[k] - xh * m2[k]);
         }
         const uint4 v = f32_to_bf16x8(o);
         dz[i] = v;
@@ -2894,7 +2911,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
         }
         {
             MSF_PROF("train_bn_apply", st);
-            bn_apply_relu_kernel<<<152 * 8, 256, 0, st>>>(w.z[l], (uint4*)w.act[l + 1], bnp,
+            bn_apply_relu_kernel<<<EW_BLOCKS, 256, 0, st>>>(w.z[l], (uint4*)w.act[l + 1], bnp,
                                                           c->d_params + o.gamma[l], c->d_params + o.beta[l], n8);
             MSF_LAUNCH_CHECK();
         }
