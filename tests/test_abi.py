@@ -62,6 +62,29 @@ def test_argument_errors_before_launch(lib):
     assert lib.msf_version().startswith(b"msf-gb300")
 
 
+def test_empty_and_negative_sizes_are_argument_errors(lib):
+    """Empty volumes, detectors, view sets, CNN workspaces and batches are
+    refused with MSF_ERR_ARG before any device call (so this runs without a GPU)."""
+    from paper_2008_01567_gb300 import msf
+    h = ctypes.c_void_p()
+
+    def create(nx=8, nt=1, nu=8, nv=8, views=3):
+        ang = np.zeros(max(views * nt, 1))
+        geom = msf.msf_geom(nu, nv, views, 0.1, 0.1, 4.0, 8.0, ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        vol = msf.msf_vol(nx, nx, nx, nt, 1.0 / max(nx, 1))
+        return lib.msf_projector_create(ctypes.byref(geom), ctypes.byref(vol), ctypes.byref(h))
+
+    for bad in (dict(nx=0), dict(nx=-3), dict(nt=0), dict(nu=0), dict(nv=0), dict(views=0)):
+        assert create(**bad) == 1, bad
+        assert b"positive" in lib.msf_last_error(), (bad, lib.msf_last_error())
+    assert lib.msf_cnn_create(0, ctypes.byref(h)) == 1
+    assert lib.msf_cnn_create(-5, ctypes.byref(h)) == 1
+    assert lib.msf_mace_batch_create(None, 0, ctypes.byref(h)) == 1
+    for fn in ("msf_dataprox_create", "msf_map_create", "msf_fixcorr_create", "msf_mace_create"):
+        assert getattr(lib, fn)(None, ctypes.byref(h)) == 1, fn
+        assert b"NULL" in lib.msf_last_error(), fn
+
+
 def test_static_projection_checks_every_column(lib):
     """msf_project_static checks on the host, before any device call, that the
     voxel planes of every (view, column) lie between source and detector; the
