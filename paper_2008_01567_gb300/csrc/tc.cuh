@@ -50,19 +50,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete is
+// parked (woken when the phase completes, or after about hint_ns) instead of
+// returning at once, so a waiting warp does not keep re-reading the barrier.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for the phase with the given parity to complete.  Gives up (returns
-// false) when *abort becomes non-zero or after `limit_ns` nanoseconds.
+// false) when *abort becomes non-zero or after `limit_ns` nanoseconds.  Each
+// retry parks the thread for up to 20 us (mbar_try_wait_suspend), so the
+// barrier and the abort flag are read rarely while a wait lasts.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
                                           uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
-    for (uint32_t i = 0;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
+    for (;;) {
+        if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
         if (abort && *abort) return false;
-        if ((i & 63) == 63) {
-            if (globaltimer_ns() - t0 > limit_ns) return false;
-            __nanosleep(128);
-        }
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
