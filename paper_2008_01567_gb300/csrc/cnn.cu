@@ -188,6 +188,14 @@ struct PackFrames {
 
 // ---------------------------------------------------------------- tcgen05 conv
 
+// One arrival per warp on a barrier that counts warps: every lane has fenced
+// its own accesses before this call; the warp converges, then lane 0 arrives
+// (32 lanes arriving on one barrier word would serialise in shared memory).
+__device__ __forceinline__ void warp_arrive(uint64_t* bar) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) tc::mbar_arrive(bar);
+}
+
 struct TileGeom {
     int H, W, imgs;          // images of this launch (img index 0..imgs-1)
     int tiles_a, tiles_b, total;
@@ -265,7 +273,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&tfull[b], 1);
-            tc::mbar_init(&tempty[b], 128);
+            tc::mbar_init(&tempty[b], 4);     // one arrival per epilogue warp
         }
         tc::mbar_init(wbar, 1);
         *abort_flag = 0;
@@ -386,7 +394,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             for (int c = 0; c < N / 16; ++c) tc::tmem_ld16(taddr + c * 16, r + c * 16);
             tc::tmem_ld_wait();
             tc::fence_before_sync();
-            tc::mbar_arrive(&tempty[ab]);
+            warp_arrive(&tempty[ab]);
             int img, a0, b0;
             decode_tile(tg, tile, img, a0, b0);
             if (epi_stores_bf16(EPI)) {
@@ -564,7 +572,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
     uint64_t* full = bars;
     uint64_t* empty = bars + NS;
     uint64_t* ffull = bars + 2 * NS;
-    uint64_t* fempty = ffull + NF;   // all 128 producers have read a patch stage
+    uint64_t* fempty = ffull + NF;   // all four producer warps have read a patch stage
     uint64_t* tfull = fempty + NF;
     uint64_t* tempty = tfull + C::NB;
     uint64_t* wbar = tempty + C::NB;
@@ -575,17 +583,18 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
+        // full, fempty: one arrival per producer warp; tempty: per epilogue warp
         for (int s = 0; s < NS; ++s) {
-            tc::mbar_init(&full[s], 128);
+            tc::mbar_init(&full[s], 4);
             tc::mbar_init(&empty[s], 1);
         }
         for (int f = 0; f < NF; ++f) {
             tc::mbar_init(&ffull[f], 1);
-            tc::mbar_init(&fempty[f], 128);
+            tc::mbar_init(&fempty[f], 4);
         }
         for (int b = 0; b < C::NB; ++b) {
             tc::mbar_init(&tfull[b], 1);
-            tc::mbar_init(&tempty[b], 128);
+            tc::mbar_init(&tempty[b], 4);
         }
         tc::mbar_init(wbar, 1);
         *abort_flag = 0;
@@ -632,7 +641,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
         }
     } else if (warp == C1_LOADER_WARP) {
         // ---------------- frame-patch copies: tile it into patch stage it % NF,
-        // once all 128 producers are done with that stage's previous tile
+        // once all four producer warps are done with that stage's previous tile
         if (PATCH && lane == 0) {
             int issued[NF];
             for (int f = 0; f < NF; ++f) issued[f] = 0;
@@ -726,8 +735,11 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
                 *reinterpret_cast<uint4*>(row + ((c ^ (m & 7)) << 4)) =
                     make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
             tc::fence_proxy_async_smem();
-            tc::mbar_arrive(&full[s]);
-            if (PATCH) tc::mbar_arrive(&fempty[fs]);   // this producer is done with patch stage fs
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(&full[s]);
+                if (PATCH) tc::mbar_arrive(&fempty[fs]);   // this producer warp is done with patch stage fs
+            }
         }
     } else {
         // ---------------- epilogue: group e = (warp - 6) / 4 takes tiles
@@ -748,7 +760,7 @@ conv1_fused_kernel(const __grid_constant__ CUtensorMap map_w, const __grid_const
             for (int c = 0; c < CH / 16; ++c) tc::tmem_ld16(taddr + c * 16, r + c * 16);
             tc::tmem_ld_wait();
             tc::fence_before_sync();
-            tc::mbar_arrive(&tempty[ab]);
+            warp_arrive(&tempty[ab]);
             int img, a0, b0;
             decode_c1_tile(tg, tile, img, a0, b0);
             uint32_t w[CH / 2];
@@ -855,7 +867,7 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
     uint64_t* tfull = bars + 2 * NS;
     uint64_t* tempty = tfull + 2;
     uint64_t* wbar = tempty + 2;
-    uint64_t* staged = wbar + 1;     // EPI_PART: activations of a tile staged (128 arrivals)
+    uint64_t* staged = wbar + 1;     // EPI_PART: activations of a tile staged (one arrival per epilogue warp)
     uint64_t* pfull = staged + 1;    // EPI_PART: per-tap sums of a tile in TMEM
     uint32_t* tmem_slot = (uint32_t*)(pfull + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -870,10 +882,10 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&tfull[b], 1);
-            tc::mbar_init(&tempty[b], 128);
+            tc::mbar_init(&tempty[b], 4);     // one arrival per epilogue warp
         }
         tc::mbar_init(wbar, 1);
-        tc::mbar_init(staged, 128);
+        tc::mbar_init(staged, 4);
         tc::mbar_init(pfull, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
@@ -1031,7 +1043,7 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
                 tc::tmem_ld_wait();
                 if (g == 1) {
                     tc::fence_before_sync();
-                    tc::mbar_arrive(&tempty[ab]);
+                    warp_arrive(&tempty[ab]);
                 }
                 uint32_t w[CH / 2];
 #pragma unroll
@@ -1073,7 +1085,7 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
                 // hand the staged activations to the MMA warp, then write the
                 // per-tap sums it returns; the staging is free again once they are
                 tc::fence_before_sync();
-                tc::mbar_arrive(staged);
+                warp_arrive(staged);
                 if (!tc::mbar_wait(pfull, it & 1, abort_flag)) {
                     give_up(MSF_ERR_TIMEOUT);
                     break;
