@@ -109,8 +109,8 @@ void msf_projector_destroy(msf_projector* p);
 size_t msf_projector_bytes(const msf_projector* p);
 
 /* Autotuner: times the forward projector with ray blocks of 32x4, 64x2 and
- * 16x8 (columns x rows) and the gather adjoint with voxel runs of 8, 16 and 32
- * along z on this plan's geometry, and keeps the fastest of each for the plan.
+ * 16x8 (columns x rows) and the gather adjoint with voxel runs of 8, 16, 32 and
+ * 64 along z on this plan's geometry, and keeps the fastest of each for the plan.
  * Results do not depend on the choice (same per-ray arithmetic and the same
  * per-voxel summation order).  Synchronises; allocates a temporary buffer.
  * h_choice (optional, 3 ints) receives {block columns, block rows, z-run}. */
@@ -119,7 +119,7 @@ msf_status msf_projector_autotune(msf_projector* p, void* stream, int* h_choice)
 /* Sets the same two launch shapes directly (no paper counterpart: a launch
  * parameter, for callers that want a fixed configuration, e.g. to reproduce
  * a tuned run without timing it again).  fwd_cols x fwd_rows must be 32x4,
- * 64x2 or 16x8 and adj_zrun 8, 16 or 32; anything else is MSF_ERR_ARG and
+ * 64x2 or 16x8 and adj_zrun 8, 16, 32 or 64; anything else is MSF_ERR_ARG and
  * leaves the plan unchanged.  Results do not depend on the choice. */
 msf_status msf_projector_set_tuning(msf_projector* p, int fwd_cols, int fwd_rows, int adj_zrun);
 

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
 
 enum AdjMode { ADJ_PLAIN = 0, ADJ_CG_INIT = 1, ADJ_CG_Q = 2 };
 
-// Voxels of one z-run handled by one thread of the gather: 8, 16 or 32,
+// Voxels of one z-run handled by one thread of the gather: 8, 16, 32 or 64,
 // chosen per plan (default 16).
 
 // Detector u coordinate (in pixels) of the point (x, y, .) for view (cs, sn);
@@ -968,6 +968,8 @@ static void launch_adj_zb(msf_projector* p, const float* e, float* out, const fl
         joseph_adj_kernel<MODE, 8><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
     else if (p->adj_zb == 32)
         joseph_adj_kernel<MODE, 32><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
+    else if (p->adj_zb == 64)
+        joseph_adj_kernel<MODE, 64><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
     else
         joseph_adj_kernel<MODE, 16><<<grid, block, 0, st>>>(p->d_col, p->d_trig, p->d_vflag, e, out, a1, a2, out2, partial, inv_s2, d);
 }
@@ -1485,8 +1487,8 @@ extern "C" msf_status msf_projector_set_tuning(msf_projector* p, int fwd_cols, i
     MSF_REQUIRE((fwd_cols == 32 && fwd_rows == 4) || (fwd_cols == 64 && fwd_rows == 2) ||
                     (fwd_cols == 16 && fwd_rows == 8),
                 "msf_projector_set_tuning: forward block %dx%d is not 32x4, 64x2 or 16x8", fwd_cols, fwd_rows);
-    MSF_REQUIRE(adj_zrun == 8 || adj_zrun == 16 || adj_zrun == 32,
-                "msf_projector_set_tuning: adjoint z-run %d is not 8, 16 or 32", adj_zrun);
+    MSF_REQUIRE(adj_zrun == 8 || adj_zrun == 16 || adj_zrun == 32 || adj_zrun == 64,
+                "msf_projector_set_tuning: adjoint z-run %d is not 8, 16, 32 or 64", adj_zrun);
     p->fwd_bx = fwd_cols;
     p->fwd_by = fwd_rows;
     p->adj_zb = adj_zrun;
@@ -1534,10 +1536,10 @@ extern "C" msf_status msf_projector_autotune(msf_projector* p, void* stream, int
     }
     p->fwd_bx = shapes[bi][0];
     p->fwd_by = shapes[bi][1];
-    const int zbs[3] = {8, 16, 32};
+    const int zbs[4] = {8, 16, 32, 64};
     best = 1e30f;
     int bz = 1;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         p->adj_zb = zbs[i];
         const float ms = time_it([&] { launch_adj_zb<ADJ_PLAIN>(p, p->d_sw, tmp, nullptr, nullptr, nullptr, nullptr, 0.0f, st); });
         if (ms < best) { best = ms; bz = i; }

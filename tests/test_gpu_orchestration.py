@@ -120,7 +120,7 @@ def test_autotune_keeps_results(M):
 def test_every_launch_shape_gives_the_same_results(M):
     # the forward's ray blocks and the adjoint's z-run lengths only reorganise
     # the launch: each ray keeps its arithmetic and each voxel its summation
-    # order, so all nine configurations agree bit for bit (a ragged volume, so
+    # order, so all twelve configurations agree bit for bit (a ragged volume, so
     # that runs and blocks end inside the grid)
     import torch
     scan = synth.Scan(n=44, nt=3, nu=61, nv=47, views=7)
@@ -131,7 +131,7 @@ def test_every_launch_shape_gives_the_same_results(M):
                    generator=torch.Generator("cuda").manual_seed(2))
     ref_y = ref_b = None
     for cols, rows in ((32, 4), (64, 2), (16, 8)):
-        for zrun in (8, 16, 32):
+        for zrun in (8, 16, 32, 64):
             M.msf_projector_set_tuning(P, cols, rows, zrun)
             y, b = torch.empty_like(e), torch.empty_like(x)
             M.msf_project(P, x, y)
