@@ -109,8 +109,10 @@ void msf_projector_destroy(msf_projector* p);
 size_t msf_projector_bytes(const msf_projector* p);
 
 /* Autotuner: times the forward projector with ray blocks of 32x4, 64x2 and
- * 16x8 (columns x rows) and the gather adjoint with voxel runs of 8, 16, 32 and
- * 64 along z on this plan's geometry, and keeps the fastest of each for the plan.
+ * 16x8 (columns x rows) and the gather adjoint with voxel runs of 8, 16 and 32
+ * along z (and 64 when the gather grid of 64-voxel runs is still at least 24
+ * waves of 8 blocks per SM deep) on this plan's geometry, and keeps the
+ * fastest of each for the plan.
  * Results do not depend on the choice (same per-ray arithmetic and the same
  * per-voxel summation order).  Synchronises; allocates a temporary buffer.
  * h_choice (optional, 3 ints) receives {block columns, block rows, z-run}. */
@@ -453,8 +455,9 @@ void msf_mace_destroy(msf_mace* m);
  * ordered on `stream`.
  * With prm->use_graph the whole iteration (every kernel and the residual copy)
  * is captured once on an internal stream into a CUDA graph and replayed on
- * `stream`; the graph is re-captured when the parameters or the CNN's weights
- * change.  Results are identical to the eager path. */
+ * `stream`; the graph is re-captured when the parameters, the CNN's weights
+ * or the projector's launch shapes (autotune, set_tuning) change.  Results
+ * are identical to the eager path. */
 msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, double* h_residual, void* stream);
 
 /* New measurements for a MACE problem from host memory: copies the photon

@@ -22,6 +22,9 @@ msf_status check_device();
 const msf_vol* projector_volume(const msf_projector* p);
 size_t projector_sino_size(const msf_projector* p);
 void projector_detector(const msf_projector* p, int* nu, int* nv);
+// Advances whenever the plan's launch shapes change (autotune, set_tuning), so
+// that a captured graph of launches with the old shapes is re-captured.
+uint64_t projector_tuning_gen(const msf_projector* p);
 
 // Device status word of a data-agent workspace: 0, or MSF_ERR_NUMERIC once a
 // CG or ICD scalar was non-finite (sticky).

@@ -35,6 +35,7 @@ struct msf_mace {
     cudaGraphExec_t gexec = nullptr;
     msf_mace_params gprm;
     uint64_t gcnn = 0;
+    uint64_t gtune = 0;            // projector launch shapes the graph was captured with
 };
 
 struct msf_mace_batch {
@@ -45,7 +46,7 @@ struct msf_mace_batch {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<msf_mace_params> gprm;
-    std::vector<uint64_t> gcnn;
+    std::vector<uint64_t> gcnn, gtune;
     // every problem runs the three CNN agents with the same parameters: the
     // agents of all problems then run as multi-problem persistent launches
     bool shared = false;
@@ -457,7 +458,8 @@ extern "C" msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, dou
     cudaStream_t st = as_stream(stream);
     if (prm->use_graph) {
         const uint64_t gen = cnn_generation(m->desc.cnn);
-        if (!m->gexec || !same_params(m->gprm, *prm) || m->gcnn != gen) {
+        const uint64_t tune = projector_tuning_gen(m->desc.proj);
+        if (!m->gexec || !same_params(m->gprm, *prm) || m->gcnn != gen || m->gtune != tune) {
             drop_graph(m->gexec);
             // work outside stream order first: kernel attributes, weight folding
             MSF_TRY(cnn_prepare(m->desc.cnn, st));
@@ -465,6 +467,7 @@ extern "C" msf_status msf_mace_step(msf_mace* m, const msf_mace_params* prm, dou
             MSF_TRY(capture(m->cap, &m->gexec, [&] { return enqueue_step(m, prm, m->cap); }));
             m->gprm = *prm;
             m->gcnn = gen;
+            m->gtune = tune;
         }
         MSF_TRY_CUDA(cudaGraphLaunch(m->gexec, st));
     } else {
@@ -551,7 +554,8 @@ extern "C" msf_status msf_mace_batch_step(msf_mace_batch* b, const msf_mace_para
     if (graph) {
         bool fresh = b->gexec != nullptr && (int)b->gprm.size() == n && was_shared == b->shared;
         for (int i = 0; fresh && i < n; ++i)
-            fresh = same_params(b->gprm[i], prm[i]) && b->gcnn[i] == cnn_generation(b->items[i]->desc.cnn);
+            fresh = same_params(b->gprm[i], prm[i]) && b->gcnn[i] == cnn_generation(b->items[i]->desc.cnn) &&
+                    b->gtune[i] == projector_tuning_gen(b->items[i]->desc.proj);
         if (!fresh) {
             drop_graph(b->gexec);
             for (int i = 0; i < n; ++i) MSF_TRY(cnn_prepare(b->items[i]->desc.cnn, st));
@@ -559,7 +563,11 @@ extern "C" msf_status msf_mace_batch_step(msf_mace_batch* b, const msf_mace_para
             MSF_TRY(capture(b->cap, &b->gexec, [&] { return enqueue_batch(b, prm, b->cap); }));
             b->gprm.assign(prm, prm + n);
             b->gcnn.resize(n);
-            for (int i = 0; i < n; ++i) b->gcnn[i] = cnn_generation(b->items[i]->desc.cnn);
+            b->gtune.resize(n);
+            for (int i = 0; i < n; ++i) {
+                b->gcnn[i] = cnn_generation(b->items[i]->desc.cnn);
+                b->gtune[i] = projector_tuning_gen(b->items[i]->desc.proj);
+            }
         }
         MSF_TRY_CUDA(cudaGraphLaunch(b->gexec, st));
     } else {

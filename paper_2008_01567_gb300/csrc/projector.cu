@@ -895,6 +895,7 @@ struct msf_projector {
     float* d_sw = nullptr;     // step-weighted sinogram for msf_backproject
     int fwd_bx = 32, fwd_by = 4;   // forward ray block (columns x rows)
     int adj_zb = 16;               // gather z-run length
+    uint64_t tuning_gen = 0;       // advanced whenever the launch shapes change
     size_t bytes = 0;
 };
 
@@ -1482,6 +1483,10 @@ extern "C" msf_status msf_project_static(const msf_geom* geom, const msf_vol* vo
 
 // ====================================================================== autotuning
 
+namespace msf {
+uint64_t projector_tuning_gen(const msf_projector* p) { return p ? p->tuning_gen : 0; }
+}  // namespace msf
+
 extern "C" msf_status msf_projector_set_tuning(msf_projector* p, int fwd_cols, int fwd_rows, int adj_zrun) {
     MSF_REQUIRE(p, "msf_projector_set_tuning: NULL plan");
     MSF_REQUIRE((fwd_cols == 32 && fwd_rows == 4) || (fwd_cols == 64 && fwd_rows == 2) ||
@@ -1492,6 +1497,7 @@ extern "C" msf_status msf_projector_set_tuning(msf_projector* p, int fwd_cols, i
     p->fwd_bx = fwd_cols;
     p->fwd_by = fwd_rows;
     p->adj_zb = adj_zrun;
+    ++p->tuning_gen;
     return MSF_OK;
 }
 
@@ -1536,15 +1542,26 @@ extern "C" msf_status msf_projector_autotune(msf_projector* p, void* stream, int
     }
     p->fwd_bx = shapes[bi][0];
     p->fwd_by = shapes[bi][1];
+    // z-runs of 64 halve the gather's block count; they are tried only while
+    // their grid stays at least 24 waves deep (8 blocks per SM), because with a
+    // shallower grid, run beside other problems' kernels (a batch), the longer
+    // blocks measured slower although they won when timed alone
     const int zbs[4] = {8, 16, 32, 64};
+    int nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        nsm = 0;
+    const dim3 g64 = adj_grid(p->dims, 64);
+    const bool deep64 = nsm > 0 && (double)g64.x * g64.y * g64.z >= 24.0 * 8.0 * nsm;
     best = 1e30f;
     int bz = 1;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < (deep64 ? 4 : 3); ++i) {
         p->adj_zb = zbs[i];
         const float ms = time_it([&] { launch_adj_zb<ADJ_PLAIN>(p, p->d_sw, tmp, nullptr, nullptr, nullptr, nullptr, 0.0f, st); });
         if (ms < best) { best = ms; bz = i; }
     }
     p->adj_zb = zbs[bz];
+    ++p->tuning_gen;
     if (cudaGetLastError() != cudaSuccess) st_ = fail(MSF_ERR_CUDA, "msf_projector_autotune: a trial launch failed");
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

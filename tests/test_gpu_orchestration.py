@@ -66,6 +66,25 @@ def test_graph_step_matches_eager(M):
     assert torch.equal(a["W"], b["W"]) and torch.equal(a["X"], b["X"])
 
 
+def test_graph_is_recaptured_after_a_tuning_change(M):
+    # the CG's partial sums follow the gather's z-run, so a graph that kept the
+    # old launch shapes would drift from the eager steps in the last bits
+    import torch
+    flat = M.pack_params(*synth.cnn_weights(96))
+    scan = synth.Scan(n=20, nt=5, nu=28, nv=24, views=8)
+    a = _problem(M, scan, 97, M.MSF_PRIOR_CNN, flat)
+    b = _problem(M, scan, 97, M.MSF_PRIOR_CNN, flat)
+    for it in range(4):
+        if it == 2:
+            for q in (a, b):
+                M.msf_projector_set_tuning(q["P"], 16, 8, 8)
+        ra = M.msf_mace_step(a["m"], 0.8, 0.2, [0.25] * 4, 3)
+        rb = M.msf_mace_step(b["m"], 0.8, 0.2, [0.25] * 4, 3, use_graph=True)
+        assert ra == rb, it
+    torch.cuda.synchronize()
+    assert torch.equal(a["W"], b["W"]) and torch.equal(a["X"], b["X"])
+
+
 def test_batch_of_uneven_problems_matches_individual_steps(M):
     import torch
     flat = M.pack_params(*synth.cnn_weights(93))
