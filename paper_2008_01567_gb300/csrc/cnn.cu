@@ -826,7 +826,8 @@ struct PairCfg {
     static constexpr int O_BYTES = 2 * TILE_BYTES;            // staging of group 0 and group 1
     static constexpr int BAR_BYTES = 512;                     // barriers, TMEM slot, abort flag (256 B), bias (256 B)
     static constexpr int SMEM = 1024 + NS * STAGE_BYTES + W_BYTES + W10_BYTES + O_BYTES + BAR_BYTES;
-    static_assert((2 * NS + 7) * 8 + 8 <= 256, "barrier block overflows into the bias");
+    static constexpr int NACC = 3;                            // TMEM accumulators (tiles in flight)
+    static_assert((2 * NS + 2 * NACC + 3) * 8 + 8 <= 256, "barrier block overflows into the bias");
     static_assert(SMEM <= 232448, "more dynamic shared memory than a CTA may have");
 };
 
@@ -853,8 +854,12 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
     using C = PairCfg;
     constexpr int NS = C::NS;
     constexpr uint32_t WBLK = CH * 128;   // one tap's 64 x 64 BF16 weights
-    constexpr int TMEM_PAIR = FUSED ? 4 * TMEM_COLS : 2 * TMEM_COLS;
-    constexpr uint32_t P_COL = 2 * 2 * CH;   // TMEM columns of the per-tap sums (2 groups x 16)
+    // NACC accumulators of 128 columns (the MMA warp runs up to NACC - 1 tiles
+    // ahead of the epilogue), then, for EPI_PART, the per-tap sums (2 x 16)
+    constexpr int NACC = C::NACC;
+    constexpr int TMEM_PAIR = 4 * TMEM_COLS;
+    constexpr uint32_t P_COL = NACC * 2 * CH;
+    static_assert(P_COL + 2 * 16 <= TMEM_PAIR, "TMEM columns");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
@@ -863,10 +868,10 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
     uint8_t* sO = sW10 + C::W10_BYTES;
     uint64_t* bars = (uint64_t*)(sO + C::O_BYTES);
     uint64_t* full = bars;
-    uint64_t* empty = bars + NS;
-    uint64_t* tfull = bars + 2 * NS;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* wbar = tempty + 2;
+    uint64_t* empty = full + NS;
+    uint64_t* tfull = empty + NS;
+    uint64_t* tempty = tfull + NACC;
+    uint64_t* wbar = tempty + NACC;
     uint64_t* staged = wbar + 1;     // EPI_PART: activations of a tile staged (one arrival per epilogue warp)
     uint64_t* pfull = staged + 1;    // EPI_PART: per-tap sums of a tile in TMEM
     uint32_t* tmem_slot = (uint32_t*)(pfull + 1);
@@ -880,7 +885,7 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             tc::mbar_init(&tfull[b], 1);
             tc::mbar_init(&tempty[b], 4);     // one arrival per epilogue warp
         }
@@ -938,6 +943,21 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
                         tc::tma_load_5d(dst + bx * PBOX_BYTES, src.map_a(job), &full[s], 0, b0 + bx - 1, p, a0 / 2 - p, img);
                     issued[s] = u + 1;
                 }
+                // the next tile of this CTA into L2 while this one computes, so that its
+                // loads, issued once a stage frees, do not wait for DRAM (the outer dx
+                // boxes cover the middle one)
+                const int nxt = tile + (int)gridDim.x;
+                if (ok && nxt < src.total()) {
+                    typename Src::Cursor pc = cur;
+                    const int pjob = src.locate(nxt, pc);
+                    int pimg, pa0, pb0;
+                    decode_pair_tile(src.geom(pjob), pc.local, pimg, pa0, pb0);
+#pragma unroll
+                    for (int p = 0; p < 2; ++p)
+#pragma unroll
+                        for (int bx = 0; bx < 3; bx += 2)
+                            tc::tma_prefetch_5d(src.map_a(pjob), 0, pb0 + bx - 1, p, pa0 / 2 - p, pimg);
+                }
             }
             if (!ok) {
                 give_up(MSF_ERR_TIMEOUT);
@@ -969,7 +989,7 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
             };
             int it = 0, j = 0;
             for (int tile = blockIdx.x; ok && tile < src.total(); tile += gridDim.x, ++it) {
-                const int ab = it & 1, ua = it >> 1;
+                const int ab = it % NACC, ua = it / NACC;
                 if (ua > 0 && !tc::mbar_wait(&tempty[ab], (ua - 1) & 1, abort_flag)) { ok = false; break; }
                 tc::fence_after_sync();
                 const uint32_t d = tmem_base + ab * 2 * CH;
@@ -1024,7 +1044,7 @@ __device__ __forceinline__ void conv_pair_body(const Src& src, const CUtensorMap
         int it = 0;
         typename Src::Cursor cur;
         for (int tile = blockIdx.x; tile < src.total(); tile += gridDim.x, ++it) {
-            const int ab = it & 1, ua = it >> 1;
+            const int ab = it % NACC, ua = it / NACC;
             if (!tc::mbar_wait(&tfull[ab], ua & 1, abort_flag)) {
                 give_up(MSF_ERR_TIMEOUT);
                 break;
