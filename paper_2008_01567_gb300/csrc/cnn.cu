@@ -324,6 +324,18 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                     }
                     issued[s] = u + 1;
                 }
+                // the CTA's next tile into L2 while this one computes (the outer dx
+                // boxes of a 3x3 tile cover the middle one)
+                if (ok && tile + (int)gridDim.x < tg.total) {
+                    int nimg, na0, nb0;
+                    decode_tile(tg, tile + (int)gridDim.x, nimg, na0, nb0);
+                    if (TAPS == 9) {
+                        tc::tma_prefetch_4d(&map_a, 0, nb0 - 1, na0 - 1, nimg);
+                        tc::tma_prefetch_4d(&map_a, 0, nb0 + 1, na0 - 1, nimg);
+                    } else {
+                        tc::tma_prefetch_4d(&map_a, 0, nb0, na0, nimg);
+                    }
+                }
             }
             if (!ok) {
                 give_up(MSF_ERR_TIMEOUT);

@@ -117,6 +117,12 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
 
 // Brings a tile of the tensor into L2 ahead of its load (no shared memory is
 // written; coordinates outside the tensor prefetch nothing there).
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"((uint64_t)map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_5d(const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4) {
     asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"((uint64_t)map),
                  "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
