@@ -249,7 +249,7 @@ def algorithmic(scan, K1):
 # profiles/ of the kernel as it stands (none is listed while a kernel has
 # changed since its capture); the traffic of these kernels scales with the
 # pixel count.
-MEASURED_TRAFFIC_PER_PX = {"conv3x3_tc": (268.566784e6 + 222.036224e6) / 2097152}
+MEASURED_TRAFFIC_PER_PX = {"conv3x3_tc": (268.578048e6 + 222.245376e6) / 2097152}
 
 
 def roofline(prof, scan, K1, peaks, steps):
