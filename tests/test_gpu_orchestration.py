@@ -165,6 +165,17 @@ def test_every_launch_shape_gives_the_same_results(M):
         M.msf_projector_set_tuning(P, 32, 4, 12)
 
 
+def test_autotuner_offers_long_gather_runs_only_for_deep_grids(M):
+    # 64-voxel gather runs halve the adjoint's block count; a small plan's grid
+    # is only a few waves deep, so its autotuner must not pick them (in a batch
+    # of concurrent problems they measured slower although they won alone)
+    scan = synth.Scan(n=64, nt=4, nu=96, nv=96, views=16)
+    P = M.Projector(scan)
+    cols, rows, zrun = M.msf_projector_autotune(P)
+    assert zrun in (8, 16, 32), zrun
+    assert (cols, rows) in ((32, 4), (64, 2), (16, 8))
+
+
 def test_denoise_batch_equals_single_problems(M):
     # uneven problems through the multi-problem persistent launches: (16^3 x 4),
     # (24 x 32 x 40 x 6) and (32^3 x 3) run together; an odd height (21^3) and a
