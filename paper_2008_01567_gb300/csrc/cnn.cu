@@ -2783,7 +2783,7 @@ extern "C" msf_status msf_training_batch(const float* d_vol, const msf_vol* vol,
     MSF_REQUIRE(sigma_lo >= 0 && sigma_hi >= sigma_lo, "msf_training_batch: need 0 <= sigma_lo <= sigma_hi");
     cudaStream_t st = as_stream(stream);
     MSF_PROF("training_batch", st);
-    training_batch_kernel<<<152 * 8, 256, 0, st>>>(d_vol, vol->nx, vol->ny, vol->nz, vol->nt, B, H, W, (float)sigma_lo,
+    training_batch_kernel<<<EW_BLOCKS, 256, 0, st>>>(d_vol, vol->nx, vol->ny, vol->nz, vol->nt, B, H, W, (float)sigma_lo,
                                                    (float)sigma_hi, seed, d_noisy, d_clean);
     MSF_LAUNCH_CHECK();
     return MSF_OK;
@@ -2937,7 +2937,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     // ---------------- forward
     {
         MSF_PROF("train_pack_input", st);
-        pack_batch_kernel<<<152 * 8, 256, 0, st>>>(d_noisy, (uint4*)w.act[0], B, H, W);
+        pack_batch_kernel<<<EW_BLOCKS, 256, 0, st>>>(d_noisy, (uint4*)w.act[0], B, H, W);
         MSF_LAUNCH_CHECK();
     }
     MSF_TRY((launch_conv<1, 64, NS_1X1, EPI_RELU>(m16[0], mw[0], m4[1], w.bf, tg, sg, nullptr, nullptr, c->d_err, st)));
@@ -2970,7 +2970,7 @@ extern "C" msf_status msf_train_step(msf_cnn* c, const float* d_noisy, const flo
     // ---------------- backward
     {
         MSF_PROF("train_last_bwd", st);
-        last_dgrad_kernel<<<152 * 8, 256, 0, st>>>(w.dR, c->d_params, o.w[9], (uint4*)w.g[0], B, H, W);
+        last_dgrad_kernel<<<EW_BLOCKS, 256, 0, st>>>(w.dR, c->d_params, o.w[9], (uint4*)w.g[0], B, H, W);
         MSF_TRY(trace_record(c, TRACE_DA, 9, w.g[0], P, st));
         wgrad_last_kernel<<<dim3(9, nchunks), 256, 0, st>>>(w.dR, (const uint4*)w.act[9], w.wpart, B, H, W);
         wgrad_last_reduce_kernel<<<(9 * CH + 255) / 256, 256, 0, st>>>(w.wpart, nchunks, c->d_grad + o.w[9]);
