@@ -95,3 +95,42 @@ def test_quality_points_follow_the_iteration_count():
         assert [t["iter"] for t in traj] == [2] and len(calls) == 2
     finally:
         metrics.psnr, metrics.ssim = orig
+
+
+def test_roofline_reports_the_dominant_kernel():
+    # the kernel with the largest total time is the one reported; its rate is
+    # the per-launch algorithmic work over the average launch, its traffic the
+    # captured bytes per pixel scaled to the launch's pixel count
+    from paper_2008_01567_gb300 import synth
+    scan = synth.FULL
+    prof = {"joseph_adj": (6, 250.0), "conv3x3_tc": (100, 320.0), "conv1_tc": (10, 20.0)}
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "measured": True}
+    r = bench.roofline(prof, scan, 4, peaks, 1)
+    px = scan.n ** 3                                     # one time-point of one agent per launch
+    assert r["kernel"] == "conv3x3_tc" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["avg_launch_ms"] - 3.2) < 1e-12 and r["launches"] == 100
+    flops = 9 * 64 * 64 * 2 * px                         # 3x3 taps x 64 in x 64 out, multiply-add
+    assert abs(r["achieved"] - flops / 3.2e-3 / 1e12) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 1700.0) < 1e-12
+    assert abs(r["traffic"] - bench.MEASURED_TRAFFIC_PER_PX["conv3x3_tc"] * px) < 1.0
+    assert 13.0e9 < r["traffic"] < 14.5e9                 # below the 256 B/px of one read and one write
+    assert abs(r["share"] - 320.0 / 590.0) < 1e-12
+    assert r["peak_source"].startswith("measured")
+
+
+def test_projector_roofline_binds_on_the_larger_floor():
+    from paper_2008_01567_gb300 import synth
+    scan = synth.Scan(n=16, nt=2, nu=24, nv=20, views=4)
+    peaks = {"hbm_gbs": 6800.0}
+    r = bench.projector_roofline(scan, 0.01, 0.02, 2000.0, peaks)
+    X = r["crossings_in_grid"]
+    assert 0 < X <= r["crossings_nominal"]
+    for name, ms in (("joseph_fwd", 0.01), ("joseph_adj", 0.02)):
+        k = r[name]
+        floors = (k["fp32_floor_ms"], k["l1_floor_ms"])
+        assert k["binding"] == ("l1" if floors[1] >= floors[0] else "fp32")
+        assert abs(k["binding_frac"] - max(floors) / ms) < 1e-12
+        assert abs(k["G_crossings_per_s"] - X / (ms / 1e3) / 1e9) < 1e-9
+    # the adjoint's model moves more bytes and instructions per crossing than the forward's
+    assert r["joseph_adj"]["l1_floor_ms"] > r["joseph_fwd"]["l1_floor_ms"]
+    assert r["joseph_adj"]["fp32_floor_ms"] > r["joseph_fwd"]["fp32_floor_ms"]
