@@ -188,11 +188,15 @@ __device__ __forceinline__ void planes_within(float f0, float b, float lo, float
 //   FWD_RESIDUAL: out = step * Lambda * (meas - A x)
 // (the CG modes write the step-weighted sinogram e' = step * e that the gather
 // adjoint consumes)
-template <int MODE>
+// PAR (the ICD agent's projection of a group step): x is zero outside one
+// voxel parity group, so an x-major ray only visits planes x = kpx (mod 2) and
+// a y-major ray planes y = kpy (mod 2); the skipped planes would each add an
+// exact zero, so the result equals the full projection bit for bit.
+template <int MODE, bool PAR = false>
 __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     const float2* __restrict__ px, const float2* __restrict__ py, const float4* __restrict__ col,
     float* __restrict__ out, const float* __restrict__ lam, const float* __restrict__ meas,
-    ProjDims d) {
+    ProjDims d, int kpx = 0, int kpy = 0) {
     const int iu = blockIdx.x * blockDim.x + threadIdx.x;
     const int iv0 = (blockIdx.y * blockDim.y + threadIdx.y) * FWD_R;
     const int g = blockIdx.z;
@@ -275,8 +279,10 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
                 acc[r] = __fadd_rn(acc[r], __fmaf_rn(wz1, __fsub_rn(bot, top), top));
             }
         };
-        for (int k = K0; k < F0; ++k) checked(k);
-        for (int k = F0; k <= F1; ++k) {
+        const int kp = xmaj ? kpx : kpy;
+        for (int k = K0; k < F0; ++k)
+            if (!PAR || (k & 1) == kp) checked(k);
+        for (int k = PAR ? F0 + ((F0 ^ kp) & 1) : F0; k <= F1; k += PAR ? 2 : 1) {
             const float tk = __fsub_rn((float)k, cmaj);
             const float fa = __fmaf_rn(tk, c.ba, c.fa_mid);
             const float a0f = floorf(fa);
@@ -295,7 +301,8 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
                 acc[r] = __fadd_rn(acc[r], __fmaf_rn(wz1, __fsub_rn(bot, top), top));
             }
         }
-        for (int k = F1 + 1; k <= K1; ++k) checked(k);
+        for (int k = F1 + 1; k <= K1; ++k)
+            if (!PAR || (k & 1) == kp) checked(k);
     }
 #pragma unroll
     for (int r = 0; r < FWD_R; ++r) {
@@ -952,6 +959,20 @@ static msf_status launch_fwd(msf_projector* p, int mode, const float* x, float* 
     return MSF_OK;
 }
 
+// A x for an x that is zero outside the voxels with x = kpx and y = kpy (mod 2)
+// (the ICD agent's group step), visiting only the planes that can touch them.
+static msf_status launch_fwd_parity(msf_projector* p, const float* x, float* out, int kpx, int kpy, cudaStream_t st) {
+    MSF_TRY(launch_pairs(p, x, st));
+    const ProjDims& d = p->dims;
+    dim3 block(p->fwd_bx, p->fwd_by);
+    dim3 grid = fwd_grid(d, block);
+    MSF_PROF("joseph_fwd", st);
+    joseph_fwd_kernel<FWD_PLAIN, true><<<grid, block, 0, st>>>(p->d_px, p->d_py, p->d_col, out, nullptr, nullptr, d,
+                                                               kpx, kpy);
+    MSF_LAUNCH_CHECK();
+    return MSF_OK;
+}
+
 static int adj_nzb(const ProjDims& d, int zb) { return (d.nz + zb - 1) / zb; }
 static dim3 adj_grid(const ProjDims& d, int zb) { return dim3((d.nx + 31) / 32, (d.ny + 3) / 4, adj_nzb(d, zb) * d.nt); }
 // partial sums per frame of an adjoint launch
@@ -1259,7 +1280,8 @@ extern "C" msf_status msf_prox_data_icd(msf_dataprox* dp, const float* d_y, cons
                                                                       inv_s2, G, d);
                 MSF_LAUNCH_CHECK();
             }
-            MSF_TRY(launch_fwd(p, FWD_PLAIN, dp->d_p, dp->d_s2, nullptr, nullptr, st));   // A delta
+            // A delta: delta is zero outside the group (icd_update clears it)
+            MSF_TRY(launch_fwd_parity(p, dp->d_p, dp->d_s2, G.px, G.py, st));
             {
                 MSF_PROF("icd_sino", st);
                 icd_sino_kernel<0><<<dim3(ICD_SINO_BLOCKS, nt), 256, 0, st>>>(p->d_col, dp->d_s2, d_lambda, dp->d_s,
