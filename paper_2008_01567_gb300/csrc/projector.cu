@@ -190,8 +190,10 @@ __device__ __forceinline__ void planes_within(float f0, float b, float lo, float
 // adjoint consumes)
 // PAR (the ICD agent's projection of a group step): x is zero outside one
 // voxel parity group, so an x-major ray only visits planes x = kpx (mod 2) and
-// a y-major ray planes y = kpy (mod 2); the skipped planes would each add an
-// exact zero, so the result equals the full projection bit for bit.
+// a y-major ray planes y = kpy (mod 2), and on a visited plane it loads only
+// the z-pair of the minor-axis tap with the group's parity (the other is zero);
+// the skipped terms are exact zeros, so the result equals the full projection
+// bit for bit.
 template <int MODE, bool PAR = false>
 __global__ void __launch_bounds__(128) joseph_fwd_kernel(
     const float2* __restrict__ px, const float2* __restrict__ py, const float4* __restrict__ col,
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
                 acc[r] = __fadd_rn(acc[r], __fmaf_rn(wz1, __fsub_rn(bot, top), top));
             }
         };
-        const int kp = xmaj ? kpx : kpy;
+        const int kp = xmaj ? kpx : kpy, ka = xmaj ? kpy : kpx;
         for (int k = K0; k < F0; ++k)
             if (!PAR || (k & 1) == kp) checked(k);
         for (int k = PAR ? F0 + ((F0 ^ kp) & 1) : F0; k <= F1; k += PAR ? 2 : 1) {
@@ -288,13 +290,16 @@ __global__ void __launch_bounds__(128) joseph_fwd_kernel(
             const float a0f = floorf(fa);
             const float wa1 = __fsub_rn(fa, a0f);
             const float2* pk = vol + k * na + (int)a0f;
+            const bool lo = (((int)a0f) & 1) == ka;   // PAR: the tap at a0 has the group's parity
 #pragma unroll
             for (int r = 0; r < FWD_R; ++r) {
                 const float fz = __fmaf_rn(tk, rz[r].bz, rz[r].fz_mid);
                 const float z0f = floorf(fz);
                 const float wz1 = __fsub_rn(fz, z0f);
                 const float2* p0 = pk + (ptrdiff_t)((int)z0f) * zs;
-                const float2 q0 = __ldg(p0), q1 = __ldg(p0 + 1);
+                const float2 zero = make_float2(0.0f, 0.0f);
+                const float2 q0 = (!PAR || lo) ? __ldg(p0) : zero;
+                const float2 q1 = (!PAR || !lo) ? __ldg(p0 + 1) : zero;
                 const float v00 = q0.x, v10 = q0.y, v01 = q1.x, v11 = q1.y;
                 const float top = __fmaf_rn(wa1, __fsub_rn(v01, v00), v00);
                 const float bot = __fmaf_rn(wa1, __fsub_rn(v11, v10), v10);
