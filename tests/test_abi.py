@@ -31,6 +31,23 @@ def test_header_declares_the_path(lib):
         assert required in names
 
 
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_header_is_plain_c_and_cpp(tmp_path, lang):
+    # the boundary is a C ABI: the header alone must compile as strict C99 and
+    # as C++ (no torch or CUDA types in any signature)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "msf.h"\nint main(void) { return 0; }\n')
+    flags = ["-std=c99", "-pedantic"] if lang == "c" else ["-std=c++17", "-x", "c++"]
+    r = subprocess.run([cc, *flags, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_every_declared_symbol_is_exported(lib):
     from paper_2008_01567_gb300 import msf
     for name in _declared():
