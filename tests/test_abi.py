@@ -48,6 +48,44 @@ def test_header_is_plain_c_and_cpp(tmp_path, lang):
     assert r.returncode == 0, r.stderr
 
 
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "msf.h"
+int main(void) {
+    msf_projector* p = 0;
+    msf_cnn* c = 0;
+    if (strncmp(msf_version(), "msf-gb300", 9) != 0) return 1;
+    /* argument errors come back as status codes before any device call */
+    if (msf_projector_create(0, 0, &p) != MSF_ERR_ARG || p != 0) return 2;
+    if (strstr(msf_last_error(), "NULL") == 0) return 3;
+    if (msf_cnn_create(0, &c) != MSF_ERR_ARG || c != 0) return 4;
+    printf("%s\n", msf_last_error());
+    return 0;
+}
+"""
+
+
+def test_library_links_and_runs_from_c(lib, tmp_path):
+    # the boundary without Python: a C program linked against libmsf.so
+    import shutil
+    import subprocess
+    from paper_2008_01567_gb300 import msf
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    libdir = os.path.dirname(msf.LIB_PATH)
+    src, exe = tmp_path / "caller.c", tmp_path / "caller"
+    src.write_text(C_CALLER)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-L", libdir, "-lmsf", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
+    assert "max_pixels" in run.stdout
+
+
 def test_every_declared_symbol_is_exported(lib):
     from paper_2008_01567_gb300 import msf
     for name in _declared():
